@@ -1,0 +1,101 @@
+"""Independent constructions used to pin the oracle (not the oracle itself).
+
+Each helper reaches a quantity by a different route from the oracle's code:
+spectral (sine-basis) matrices instead of stencil loops, numpy polynomial
+integration instead of Lagrange-coefficient expansion, closed-form ODE
+solutions instead of time stepping.
+"""
+from __future__ import annotations
+
+import numpy as np
+from numpy.polynomial import polynomial as P
+
+
+def eig_1d(N: int, order: int, k):
+    """Eigenvalue of the 1-D second-difference operator on sin(k pi x), h = 1/(N+1).
+
+    order 2: (2 cos(theta) - 2) / h^2;  order 4 (wide, odd reflection):
+    (-2 cos(2 theta) + 32 cos(theta) - 30) / (12 h^2), theta = k pi h.
+    """
+    h = 1.0 / (N + 1)
+    th = np.asarray(k, dtype=np.float64) * np.pi * h
+    if order == 2:
+        return (2.0 * np.cos(th) - 2.0) / h**2
+    return (-2.0 * np.cos(2 * th) + 32.0 * np.cos(th) - 30.0) / (12.0 * h**2)
+
+
+def dst_basis(N: int):
+    """Orthonormal sine basis: column k-1 is sqrt(2h) sin(k pi x_i)."""
+    h = 1.0 / (N + 1)
+    i = np.arange(1, N + 1)
+    return np.sqrt(2.0 * h) * np.sin(np.outer(i, i) * np.pi * h)
+
+
+def lap_1d_dense(N: int, order: int):
+    """The 1-D operator as V diag(lambda) V^T (exact: sines are its eigenvectors)."""
+    V = dst_basis(N)
+    lam = eig_1d(N, order, np.arange(1, N + 1))
+    return V @ np.diag(lam) @ V.T
+
+
+def A_dense(N: int, order: int, c: float):
+    """I - c (L (x) I (x) I + I (x) L (x) I + I (x) I (x) L) on the z,y,x-ordered vector."""
+    L = lap_1d_dense(N, order)
+    I = np.eye(N)
+    lap = np.kron(np.kron(L, I), I) + np.kron(np.kron(I, L), I) + np.kron(np.kron(I, I), L)
+    return np.eye(N**3) - c * lap
+
+
+def gl_nodes_legendre(M: int):
+    """Gauss-Lobatto nodes on [0,1]: ends plus roots of P'_{M-1} (numpy legendre)."""
+    from numpy.polynomial import legendre as Lg
+    c = np.zeros(M)
+    c[M - 1] = 1.0
+    r = np.sort(np.real(Lg.legroots(Lg.legder(c))))
+    x = np.concatenate([[-1.0], r, [1.0]])
+    return 0.5 * (x + 1.0)
+
+
+def qmatrix_numpy(tau):
+    """Q[m][j] = int_0^{tau_m} l_j(s) ds via numpy polyfit of the Lagrange data."""
+    M = len(tau)
+    Q = np.zeros((M, M))
+    for j in range(M):
+        y = np.zeros(M)
+        y[j] = 1.0
+        coef = np.polyfit(tau, y, M - 1)[::-1]  # low -> high
+        integ = P.polyint(coef)
+        for m in range(M):
+            Q[m, j] = P.polyval(tau[m], integ)
+    return Q
+
+
+def forcing_g(t, nu, kappa):
+    return -(np.sin(t) - kappa * nu * np.pi**2 * np.cos(t))
+
+
+def scalar_collocation(lam, a0, t0, dt, nu, kappa, forcing=True):
+    """Solve the M=5 or M=3 collocation system of a' = lam a + g(t) exactly.
+
+    a_m = a0 + dt sum_j Q[m][j] (lam a_j + g(t_j)), a dense (M x M) linear solve.
+    Returns a function M -> node values."""
+    def solve(M):
+        tau = gl_nodes_legendre(M)
+        Q = qmatrix_numpy(tau)
+        g = forcing_g(t0 + dt * tau, nu, kappa) if forcing else np.zeros(M)
+        A = np.eye(M) - dt * lam * Q
+        rhs = a0 * np.ones(M) + dt * Q @ g
+        return np.linalg.solve(A, rhs)
+    return solve
+
+
+def semidiscrete_amplitude(lam, t, nu, kappa, a0=1.0):
+    """Exact solution of a' = lam a + g(t), g = -(sin t - kappa nu pi^2 cos t), a(0) = a0.
+
+    With c = -lam, d = kappa nu pi^2: a = A cos t + B sin t + (a0 - A) e^{-c t},
+    A = (1 + c d)/(1 + c^2), B = (d - c)/(1 + c^2)."""
+    c = -lam
+    d = kappa * nu * np.pi**2
+    A = (1.0 + c * d) / (1.0 + c * c)
+    B = (d - c) / (1.0 + c * c)
+    return A * np.cos(t) + B * np.sin(t) + (a0 - A) * np.exp(-c * t)

@@ -1,0 +1,233 @@
+"""Pins of the oracle's collocation, SDC, MLSDC and PFASST emulation (CPU only).
+
+Paper: Sec. 1.1 (collocation formula, IMEX-Euler sweep, spectral quadrature,
+order from the number of sweeps, MLSDC and PFASST), Eqs. 3-4 (forcing and
+analytic solution).
+"""
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_1307_7867_gb300 import inputs
+from tests import independent as ind
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden_gl():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "gauss_lobatto.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        M, node, w = line.split()
+        node = eval(node, {"sqrt": np.sqrt})
+        rows.append((int(M), float(node), float(Fraction(w))))
+    return rows
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5])
+def test_gl_nodes_are_lobatto(oracle, M):
+    assert np.abs(oracle.gl_nodes(M) - ind.gl_nodes_legendre(M)).max() <= 1e-15
+
+
+def test_q_last_row_is_lobatto_weights(oracle):
+    """Q[M-1] (the integral over the whole step) equals the printed Lobatto weights."""
+    g = _golden_gl()
+    for M in (3, 5):
+        nodes = np.array([n for m, n, w in g if m == M])
+        weights = np.array([w for m, n, w in g if m == M])
+        assert np.abs(oracle.gl_nodes(M) - nodes).max() <= 1e-15
+        assert np.abs(oracle.qmatrix(M)[M - 1] - weights).max() <= 4e-15  # monomial-basis rounding
+
+
+def test_q_three_nodes_exact_rationals(oracle):
+    Q = oracle.qmatrix(3)
+    ref = np.array([[0, 0, 0], [Fraction(5, 24), Fraction(1, 3), Fraction(-1, 24)],
+                    [Fraction(1, 6), Fraction(2, 3), Fraction(1, 6)]], dtype=float)
+    assert np.abs(Q - ref).max() <= 2.3e-16  # one ulp of 2/3
+
+
+@pytest.mark.parametrize("M", [2, 3, 4, 5])
+def test_q_polynomial_exactness_and_s(oracle, M):
+    """sum_j Q[m][j] tau_j^p = tau_m^{p+1}/(p+1) for p <= M-1; Q equals the numpy
+    construction; S is the row difference of Q with row sums tau_{m+1}-tau_m."""
+    tau = oracle.gl_nodes(M)
+    Q = oracle.qmatrix(M)
+    for p in range(M):
+        assert np.abs(Q @ tau**p - tau ** (p + 1) / (p + 1)).max() <= 1e-14
+    assert np.abs(Q - ind.qmatrix_numpy(tau)).max() <= 1e-13
+    S = oracle.smatrix(M)
+    assert np.abs(S - np.diff(Q, axis=0)).max() <= 1e-16
+    assert np.abs(S.sum(axis=1) - np.diff(tau)).max() <= 1e-14
+
+
+PROB_TIGHT = dict(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-14, mg_max=200)
+
+
+@pytest.mark.parametrize("order,M,k", [(2, 3, (1, 1, 1)), (4, 5, (1, 1, 1)), (4, 3, (2, 1, 3))])
+def test_sdc_converges_to_collocation_of_mode(oracle, order, M, k):
+    """For a single sine mode, SDC iterated to convergence equals the scalar
+    collocation solution a_m (dense M x M solve), times the mode."""
+    N, dt, t0 = 7, 0.125, 0.25
+    prob = oracle.Prob(**PROB_TIGHT)
+    if k != (1, 1, 1):
+        prob.forcing = 0  # the forcing lives on the (1,1,1) mode only
+    u0 = inputs.sine_mode(N, *k)
+    U, F = oracle.spread(N, order, M, prob, u0)
+    for _ in range(40):
+        U, F, rc, st = oracle.sdc_sweep(N, order, M, prob, t0, dt, U, F)
+        assert rc == oracle.OK
+    lam = 0.1 * sum(ind.eig_1d(N, order, ka) for ka in k)
+    a = ind.scalar_collocation(lam, 1.0, t0, dt, 0.1, 1.0, forcing=prob.forcing == 1)(M)
+    err = max(np.abs(U[m] - a[m] * u0).max() for m in range(M))
+    assert err <= 1e-12
+    assert oracle.sdc_residual(N, order, M, prob, t0, dt, U, F) <= 1e-12
+
+
+@pytest.mark.parametrize("M,sweeps", [(3, 1), (3, 2), (3, 3), (5, 2), (5, 3)])
+def test_sdc_temporal_order(oracle, M, sweeps):
+    """k sweeps of IMEX Euler give order min(k, 2M-2) (Sec. 1.1), measured
+    against the exact semi-discrete solution of one mode."""
+    N, order, T = 3, 2, 0.5
+    prob = oracle.Prob(**PROB_TIGHT)
+    u0 = inputs.sine_mode(N)
+    lam = 0.1 * 3 * ind.eig_1d(N, order, 1)
+    exact = ind.semidiscrete_amplitude(lam, T, 0.1, 1.0) * u0
+    errs = []
+    for nsteps in (4, 8, 16):
+        uT, rc, _ = oracle.sdc_run(N, order, M, prob, T / nsteps, nsteps, sweeps, u0)
+        errs.append(np.abs(uT - exact).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    expect = min(sweeps, 2 * M - 2)
+    assert abs(rates[-1] - expect) <= 0.35, (errs, rates)
+
+
+@pytest.mark.parametrize("order,expect", [(2, 2.0), (4, 4.0)])
+def test_spatial_order_against_analytic(oracle, order, expect):
+    """With the time error negligible (converged 5-node collocation), the error
+    against u = Phi cos t (Eq. 4, exact forcing kappa = 3) falls like h^order."""
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=3.0, mg_tol=1e-13, mg_max=100)
+    errs = []
+    for N in (3, 7, 15):
+        u0 = inputs.sine_mode(N)
+        uT, rc, _ = oracle.sdc_run(N, order, 5, prob, 0.125, 1, 12, u0, tol=1e-13)
+        errs.append(np.abs(uT - np.cos(0.125) * u0).max())
+    rate = np.log2(errs[1] / errs[2])
+    assert abs(rate - expect) <= 0.3, errs
+
+
+def test_forcing_as_printed_has_its_closed_form(oracle):
+    """With Eq. 3 as printed (kappa = 1) the mode amplitude follows
+    a' = lam_h a - (sin t - nu pi^2 cos t): the run matches that ODE's exact
+    solution, and differs from cos t (Eq. 4 needs kappa = 3)."""
+    N, order = 7, 4
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    u0 = inputs.sine_mode(N)
+    uT, rc, _ = oracle.sdc_run(N, order, 5, prob, 0.125, 2, 12, u0, tol=1e-13)
+    lam = 0.1 * 3 * ind.eig_1d(N, order, 1)
+    a = ind.semidiscrete_amplitude(lam, 0.25, 0.1, 1.0)
+    assert np.abs(uT - a * u0).max() <= 1e-11
+    assert np.abs(uT - np.cos(0.25) * u0).max() > 1e-2
+
+
+def test_fas_leaves_fine_collocation_solution_fixed(oracle):
+    """If the fine level holds its collocation solution, the FAS-corrected
+    coarse sweep returns the restricted state unchanged and the interpolated
+    correction is zero (to solver tolerance)."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    prob = oracle.Prob(**PROB_TIGHT)
+    dt, t0 = 1.0 / 16, 0.5
+    u0 = inputs.smooth_random_field(15, seed=4, kmax=4)
+    U, F = oracle.spread(*fine, prob, u0)
+    for _ in range(30):
+        U, F, rc, _ = oracle.sdc_sweep(*fine, prob, t0, dt, U, F)
+    assert oracle.sdc_residual(*fine, prob, t0, dt, U, F) <= 1e-12
+    UG, FG, UGr, tQ = oracle.fas_restrict(fine, coarse, prob, t0, dt, U, F)
+    assert oracle.sdc_residual(*coarse, prob, t0, dt, UG, FG, tQ) <= 1e-11
+    UG2, FG2, rc, _ = oracle.sdc_sweep(*coarse, prob, t0, dt, UG, FG, tQ)
+    assert np.abs(UG2 - UGr).max() <= 1e-11
+    U2, F2 = oracle.fas_interpolate(fine, coarse, prob, UG2, UGr, U)
+    assert np.abs(U2 - U).max() <= 1e-11
+
+
+def test_fas_without_tau_breaks_the_fixed_point(oracle):
+    """Dropping tau (a plausible mistake) moves the converged state: the
+    fixed-point test above would catch it."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    prob = oracle.Prob(**PROB_TIGHT)
+    dt, t0 = 1.0 / 16, 0.5
+    U, F = oracle.spread(*fine, prob, inputs.smooth_random_field(15, seed=4, kmax=4))
+    for _ in range(30):
+        U, F, rc, _ = oracle.sdc_sweep(*fine, prob, t0, dt, U, F)
+    UG, FG, UGr, tQ = oracle.fas_restrict(fine, coarse, prob, t0, dt, U, F)
+    UG2, _, _, _ = oracle.sdc_sweep(*coarse, prob, t0, dt, UG, FG, None)
+    assert np.abs(UG2 - UGr).max() > 1e-6
+
+
+def test_mlsdc_converges_to_sdc_collocation(oracle):
+    """MLSDC to residual 1e-12 and SDC to 1e-12 reach the same fine collocation
+    solution."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    u0 = inputs.sine_mode(15)
+    a, rc, st = oracle.mlsdc_run(fine, coarse, prob, 1 / 16, 2, u0, max_iters=60, tol=1e-12)
+    b, rc2, _ = oracle.sdc_run(*fine, prob, 1 / 16, 2, 60, u0, tol=1e-12)
+    assert rc == oracle.OK and rc2 == oracle.OK
+    assert np.abs(a - b).max() <= 1e-10
+
+
+def test_pfasst_single_slice_is_mlsdc(oracle):
+    """PFASST on one time slice is MLSDC (Sec. 2.1)."""
+    fine, coarse = (7, 4, 5), (3, 2, 3)
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-12, mg_max=100)
+    u0 = inputs.smooth_random_field(7, seed=6, kmax=3)
+    a, _, sa = oracle.pfasst_run(fine, coarse, prob, 1 / 8, 3, 1, u0, nsweeps_fine=2, max_iters=4)
+    b, _, sb = oracle.mlsdc_run(fine, coarse, prob, 1 / 8, 3, u0, nsweeps_fine=2, max_iters=4,
+                                tol=-1.0)
+    assert np.abs(a - b).max() <= 1e-15
+    assert sa["vcycles"] == sb["vcycles"]
+
+
+def test_pfasst_converges_to_serial_collocation(oracle):
+    """Iterated until converged, PFASST over P slices equals the serial fine
+    collocation solution, step by step."""
+    fine, coarse = (7, 4, 5), (3, 2, 3)
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    u0 = inputs.sine_mode(7)
+    a, rc, st = oracle.pfasst_run(fine, coarse, prob, 1 / 16, 8, 8, u0, max_iters=60, tol=1e-12)
+    b, _, _ = oracle.sdc_run(*fine, prob, 1 / 16, 8, 60, u0, tol=1e-12)
+    assert st["residual"] <= 1e-12
+    assert np.abs(a - b).max() <= 1e-10
+    # after only 2 iterations the later slices are not converged yet
+    c, _, st2 = oracle.pfasst_run(fine, coarse, prob, 1 / 16, 8, 8, u0, max_iters=2)
+    assert st2["slice_residuals"][-1] > st2["slice_residuals"][0]
+
+
+def test_fas_interpolation_reproduces_quadratic_in_time(oracle):
+    """A coarse correction that is quadratic in time times a coarse field e
+    reaches fine node j as q(tau_j) * (piecewise-linear interpolant of e):
+    quadratic Lagrange interpolation through 3 nodes is exact for it, and the
+    space part equals numpy.interp per axis."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    prob = oracle.Prob(**PROB_TIGHT)
+    e = inputs.random_field(7, seed=21)
+    q = lambda t: 0.3 - 1.1 * t + 2.5 * t * t
+    tg, tf = ind.gl_nodes_legendre(3), ind.gl_nodes_legendre(5)
+    UGr = inputs.random_field(7, seed=22, batch=3)
+    UG = UGr + np.array([q(t) * e for t in tg])
+    UF = inputs.random_field(15, seed=23, batch=5)
+    UF2, FF2 = oracle.fas_interpolate(fine, coarse, prob, UG, UGr, UF)
+    xc = np.arange(0, 9) / 8.0
+    xf = np.arange(1, 16) / 16.0
+    t = np.pad(e, 1)
+    for ax in (2, 1, 0):
+        t = np.apply_along_axis(lambda v: np.interp(xf, xc, v), ax, t)
+    for j in range(5):
+        assert np.abs(UF2[j] - UF[j] - q(tf[j]) * t).max() <= 1e-14
+    # F is recomputed from the new U: compare with the pinned operator route
+    lam_op = ind.A_dense(15, 4, -0.1)  # I + 0.1 L  -> F = (that - I) u
+    for j in (0, 3):
+        ref = ((lam_op - np.eye(15**3)) @ UF2[j].reshape(-1)).reshape(UF2[j].shape)
+        assert np.abs(FF2[j] - ref).max() <= 1e-9 * np.abs(ref).max()
