@@ -1,0 +1,213 @@
+/*
+ * heat3d.h -- C ABI of libheat3d.so: a GB300 (sm_103a) solver for the forced
+ * 3-D heat equation  u_t = nu Delta u + f  on [0,1]^3 with u = 0 on the
+ * boundary (arXiv:1307.7867, Sec. 1, Eqs. 1-4), integrated in time by SDC,
+ * two-level MLSDC and PFASST (Sec. 1.1) with multigrid solves of the
+ * implicit-Euler substeps (Sec. 1.2).
+ *
+ * Conventions shared by every call:
+ *  - Grid functions crossing this boundary are DENSE arrays of the N^3
+ *    interior values, FP64, index ((k * N) + j) * N + i (x fastest, z
+ *    slowest), with x_i = (i + 1) h, h = 1 / (N + 1), zero Dirichlet values
+ *    on the boundary.  Inside the library fields are stored pitched.
+ *  - Pointers documented as "device" must point to device memory of the
+ *    context's device; "host or device" pointers are classified with
+ *    cudaPointerGetAttributes (pageable or pinned host memory both work).
+ *  - The caller owns every buffer it passes; the library never frees one.
+ *    Device memory for resident state comes from ONE workspace the caller
+ *    allocates (heat3d_workspace_size) and binds (heat3d_bind_workspace);
+ *    the library allocates no device memory of its own.
+ *  - Return codes: HEAT3D_OK (0) or a negative HEAT3D_E* code; a context
+ *    keeps a message for the last failure (heat3d_last_error).
+ *  - Work is enqueued on the context's CUDA stream.  Calls that read a
+ *    convergence norm synchronise that stream; pfasst_run and heat3d_wait
+ *    return with their results complete.  One host thread per context.
+ */
+#ifndef HEAT3D_H
+#define HEAT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HEAT3D_OK 0
+#define HEAT3D_EINVAL (-1)    /* bad argument or configuration */
+#define HEAT3D_ENOMEM (-2)    /* workspace too small, or a request refused admission */
+#define HEAT3D_ENOTCONV (-3)  /* a solve hit its V-cycle cap above its tolerance */
+#define HEAT3D_ENAN (-4)      /* a residual norm was NaN or Inf */
+#define HEAT3D_ETIMEOUT (-5)  /* a bounded device-side wait gave up */
+#define HEAT3D_ECUDA (-6)     /* a CUDA runtime call failed */
+#define HEAT3D_ESTATE (-7)    /* call made in the wrong state (e.g. no workspace bound) */
+
+#define HEAT3D_FP64 0   /* every field and every smoother in FP64 */
+#define HEAT3D_MIXED 1  /* FP32 V-cycles inside FP64 residual refinement */
+
+#define HEAT3D_FORCING_NONE 0          /* f = 0 */
+#define HEAT3D_FORCING_PAPER_LITERAL 1 /* Eq. 3 as printed: f = -Phi (sin t - nu pi^2 cos t) */
+#define HEAT3D_FORCING_EXACT 2         /* f = -Phi (sin t - 3 nu pi^2 cos t): u = Phi cos t solves it */
+
+#define HEAT3D_MAX_NODES 5
+
+/* One level of the space-time hierarchy (Sec. 1: PFASST coarsens nodes, mesh
+ * and stencil order). */
+typedef struct {
+  int N;     /* interior points per axis; must be 2^k - 1 (multigrid halving) */
+  int order; /* 2: 7-point Laplacian; 4: 13-point wide Laplacian (odd-reflection ghosts) */
+  int M;     /* Gauss-Lobatto nodes per step, both ends included, 2..5 */
+} heat3d_level;
+
+/* Multigrid settings for every implicit solve (Sec. 1.2). */
+typedef struct {
+  int nu1, nu2;   /* damped-Jacobi pre- and post-smoothing sweeps (V(2,1)) */
+  int max_cycles; /* cap per solve */
+  double tol;     /* stop when max|b - A u| <= tol; tol < 0: exactly max_cycles cycles */
+} heat3d_mg;
+
+typedef struct {
+  double nu;                /* diffusion coefficient */
+  double T;                 /* end time of pfasst_run */
+  double dt;                /* step (time slice) length */
+  int nlevels;              /* 1: single-level SDC; 2: MLSDC (slices = 1) or PFASST */
+  heat3d_level levels[2];   /* [0] fine, [1] coarse (N_f = 2 N_c + 1 or equal; nested nodes) */
+  int sweeps_fine;          /* fine sweeps per iteration (nlevels = 1: sweeps per step) */
+  int sweeps_coarse;        /* coarse sweeps per iteration and in the predictor */
+  int slices;               /* PFASST time slices iterated together (1 = serial) */
+  int iters;                /* MLSDC/PFASST iterations per block (cap when tol_sdc >= 0) */
+  double tol_sdc;           /* stop when the fine collocation residual <= tol_sdc; < 0: fixed */
+  int predictor;            /* 1: serial coarse predictor before the first iteration */
+  heat3d_mg mg;
+  int precision;            /* HEAT3D_FP64 or HEAT3D_MIXED */
+  int forcing;              /* HEAT3D_FORCING_* */
+  int batch;                /* state slots per level for sdc_sweep / serving (>= slices) */
+  int device;               /* CUDA device ordinal */
+  void* stream;             /* cudaStream_t for all work of this context (NULL: legacy) */
+  int use_graphs;           /* 1: replay V-cycles from captured CUDA graphs */
+} heat3d_config;
+
+typedef struct {
+  long long vcycles;   /* V-cycles (refinement steps) over all solves */
+  long long solves;    /* implicit solves */
+  long long sweeps;    /* SDC sweeps on any level (a batched sweep counts once) */
+  long long iters;     /* MLSDC / PFASST iterations */
+  long long steps;     /* time steps completed (slices count one each) */
+  int notconv;         /* solves that stopped at the cycle cap above tolerance */
+  double residual;     /* last fine-level collocation residual computed (max over items) */
+  double mg_residual;  /* last multigrid residual max|b - A u| */
+  double seconds;      /* device time of the call, from CUDA events on the stream */
+  double bytes;        /* algorithmic HBM bytes of the call's kernels (a counter) */
+} heat3d_stats;
+
+typedef struct heat3d_ctx heat3d_ctx;
+
+/* Fills a config with the paper's fine/coarse hierarchy at N = 31/15 and V(2,1). */
+void heat3d_config_default(heat3d_config* cfg);
+
+/* Bytes of device workspace a context with this config needs. */
+int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes);
+
+/* Validates cfg and builds the host-side context (hierarchy, Gauss-Lobatto
+ * nodes, integration matrices).  Allocates no device memory. */
+int heat3d_init(const heat3d_config* cfg, heat3d_ctx** out);
+
+/* Binds caller-owned device memory (>= heat3d_workspace_size, 256-byte
+ * aligned) and zeroes it on the stream.  The memory must outlive the context. */
+int heat3d_bind_workspace(heat3d_ctx* ctx, void* dptr, size_t bytes);
+
+/* Releases host resources (graphs, events); never frees the workspace. */
+int heat3d_destroy(heat3d_ctx* ctx);
+
+/* Message of the last failure on ctx (never NULL; "" when none). */
+const char* heat3d_last_error(const heat3d_ctx* ctx);
+
+/* Replaces the stream every later call enqueues on. */
+int heat3d_set_stream(heat3d_ctx* ctx, void* stream);
+
+/* out = nu * Delta_h u on level `level`'s grid (Sec. 1 method of lines;
+ * 7-point or wide stencil).  u, out: device, dense N^3 FP64. */
+int heat3d_apply_laplacian(heat3d_ctx* ctx, int level, const double* u, double* out);
+
+/* Solves (I - c Delta_h) u = rhs by V(nu1, nu2) multigrid cycles in the
+ * context's precision (Sec. 1.2; coarsening to one unknown).  u is the warm
+ * start and the result.  max_cycles/tol as in heat3d_mg.  rhs, u: device,
+ * dense N^3 FP64.  Returns HEAT3D_ENOTCONV when tol >= 0 is not reached. */
+int mg_vcycle(heat3d_ctx* ctx, int level, double c, const double* rhs, double* u, int max_cycles,
+              double tol, heat3d_stats* stats);
+
+/* Spreads the initial value u0 (host or device, dense N^3 FP64) to every
+ * node of state slot `item` on `level`, sets the slot's step start t0 and
+ * evaluates f^I at every node (the SDC initial iterate). */
+int heat3d_set_state(heat3d_ctx* ctx, int level, int item, double t0, const double* u0);
+
+/* Copies node `node` of slot `item` on `level` out to `out` (host or device)
+ * or in from `in` (host or device; f^I of that node is re-evaluated). */
+int heat3d_get_node(heat3d_ctx* ctx, int level, int item, int node, double* out);
+int heat3d_set_node(heat3d_ctx* ctx, int level, int item, int node, const double* in);
+
+/* One IMEX-Euler SDC sweep (Sec. 1.1, the sweep equation with the spectral
+ * quadrature S) on slots [batch_begin, batch_begin + batch_count) of
+ * `level`; on level 1 the slot's FAS correction (set by heat3d_fas_restrict)
+ * is included. */
+int sdc_sweep(heat3d_ctx* ctx, int level, int batch_begin, int batch_count, heat3d_stats* stats);
+
+/* Collocation residual max_m max_x |U_0 + dt Q (F + f^E) (+ tau) - U_m| of
+ * slot `item` on `level` (Sec. 1: the threshold applies to it). */
+int heat3d_sdc_residual(heat3d_ctx* ctx, int level, int item, double* residual);
+
+/* FAS coupling of slots [begin, begin + count) (Sec. 1.1): restriction of
+ * the fine state to the coarse level by injection in space and time, coarse
+ * f^I and the FAS correction tau; and the interpolation of the coarse
+ * correction back (trilinear in space, Lagrange in time) with f^I
+ * re-evaluated on the fine level. */
+int heat3d_fas_restrict(heat3d_ctx* ctx, int begin, int count);
+int heat3d_fas_interpolate(heat3d_ctx* ctx, int begin, int count);
+
+/* Integrates from t = 0 to cfg.T: single-level SDC (nlevels = 1), MLSDC
+ * (slices = 1) or PFASST on blocks of `slices` time slices (Sec. 1.1).
+ * u0 in, uT out: host or device, dense N_fine^3 FP64. */
+int pfasst_run(heat3d_ctx* ctx, const double* u0, double* uT, heat3d_stats* stats);
+
+/* ---------------------------------------------------------------------- */
+/* Serving: continuous batching of independent heat-equation solves.        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct {
+  int device;
+  void* pool;          /* device memory the server sub-allocates request state from */
+  size_t pool_bytes;   /* admission is refused (queued) while the pool has no room */
+  int max_active;      /* slots: requests resident at once */
+  int sweeps;          /* SDC sweeps per step (fixed count) */
+  int precision;       /* HEAT3D_FP64 or HEAT3D_MIXED */
+  heat3d_mg mg;
+} heat3d_server_config;
+
+typedef struct {
+  int N;                   /* interior points per axis (2^k - 1) */
+  double nu, T, dt;        /* diffusion coefficient, horizon, step */
+  int nmodes;              /* <= 8 sine modes of the initial value */
+  int k[8][3];             /* mode numbers (k1, k2, k3) */
+  double amp[8];           /* amplitudes */
+} heat3d_request;
+
+typedef struct heat3d_server heat3d_server;
+
+int heat3d_server_create(const heat3d_server_config* cfg, heat3d_server** out);
+/* Queues a request; returns at once with its ticket.  HEAT3D_ENOMEM if the
+ * request could never fit in the pool. */
+int heat3d_submit(heat3d_server* s, const heat3d_request* req, uint64_t* ticket);
+/* *done = 1 once the ticket's solve has finished. */
+int heat3d_poll(heat3d_server* s, uint64_t ticket, int* done);
+/* Blocks until the ticket finishes; copies u(T) (host or device, dense N^3
+ * FP64) and its statistics (NULL to skip either), then releases the ticket. */
+int heat3d_wait(heat3d_server* s, uint64_t ticket, double* u_out, heat3d_stats* stats);
+/* Latency percentiles (seconds, submit to completion) of finished requests. */
+int heat3d_server_latency(heat3d_server* s, double* p50, double* p99, long long* completed);
+int heat3d_server_destroy(heat3d_server* s);
+const char* heat3d_server_last_error(const heat3d_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HEAT3D_H */

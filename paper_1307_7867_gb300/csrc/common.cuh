@@ -1,0 +1,60 @@
+// common.cuh -- shared types of the heat3d CUDA library (sm_103a).
+//
+// Field layout in device memory: for a grid with N interior points per axis a
+// field is px * N * N elements, x fastest, with the x pitch px = N rounded up
+// to 4 (the 2^k - 1 grids of the hierarchy get px = 2^k, so every row starts
+// 128-byte aligned once px * sizeof(T) >= 128).  The pad columns stay zero
+// and are never read as data.  Items of a batch (PFASST slices, serving
+// requests, nodes) follow each other at the field stride fs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace h3d {
+
+constexpr int kMaxNodes = 5;
+constexpr int kMaxLevels = 12;  // multigrid levels: N up to 2^12 - 1
+
+struct Grid {
+  int N;            // interior points per axis
+  int px;           // x pitch in elements
+  long long plane;  // px * N
+  long long fs;     // field stride (elements) between consecutive items
+};
+
+inline Grid make_grid(int N) {
+  Grid g;
+  g.N = N;
+  g.px = (N + 3) / 4 * 4;
+  g.plane = (long long)g.px * N;
+  long long f = g.plane * N;
+  g.fs = (f + 63) / 64 * 64;  // keeps every field 256-byte aligned for 4- and 8-byte types
+  return g;
+}
+
+// Coefficients of A = I - c Delta_h on one multigrid level for one item:
+//   A u = d u - e S, with S = sum of the 6 nearest neighbours (7 points) or
+//   16 * (6 nearest) - (6 second neighbours) (wide stencil);
+//   wd = omega / d for damped Jacobi; a11 = A on the one-unknown grid.
+template <typename T>
+struct Coef {
+  T d, e, wd, a11;
+};
+
+// Per item, per SDC level: step data of the sweep (Sec. 1.1).
+struct ItemSDC {
+  double dtS[kMaxNodes - 1][kMaxNodes];  // dt * S[m][j]
+  double gS[kMaxNodes - 1];              // dt * sum_j S[m][j] g(t0 + dt tau_j): forcing integral
+  double dtm[kMaxNodes - 1];             // dt * (tau_{m+1} - tau_m)
+  double dtQ[kMaxNodes][kMaxNodes];      // dt * Q[m][j]  (FAS restriction, fine level)
+  double gQ[kMaxNodes];                  // dt * sum_j Q[m][j] g(t0 + dt tau_j)
+  double nu;
+};
+
+// FAS transfer data between the fine (F) and coarse (G) levels.
+struct FasMap {
+  int jm[kMaxNodes];                      // fine node of coarse node m
+  double L[kMaxNodes][kMaxNodes];         // L[j][m] = l^G_m(tau^F_j): Lagrange in time
+};
+
+}  // namespace h3d

@@ -1,0 +1,111 @@
+// kernels.cuh -- launchers of the heat3d CUDA kernels (definitions in
+// mg_kernels.cu and sdc_kernels.cu).  Every launcher enqueues on `st`,
+// operates on `B` consecutive items at field stride g.fs (pointers address
+// item 0 of the launch), skips item b when active != nullptr and active[b] == 0,
+// and returns cudaGetLastError() of the launch.
+#pragma once
+#include "common.cuh"
+
+namespace h3d {
+
+// z-marching launch shape: blocks of bx * by threads, each thread one (x, y)
+// column over zc consecutive planes.
+struct Shape {
+  int bx = 32, by = 4, zc = 16;
+};
+
+// ---- spatial operator (Sec. 1, method of lines) ----
+// out = alpha_b * L u with L = (S1 - 6u) (order 2) or (16 S1 - S2 - 90u)
+// (order 4); alpha_b = nu_b / h^2 or nu_b / (12 h^2).  When add_src != nullptr
+// also writes add_dst = u + add_src (the next substep's right-hand side).
+cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long long u_stride,
+                       double* out, long long out_stride, const double* alpha,
+                       const double* add_src, double* add_dst, long long add_stride,
+                       const int* active, Shape sh, cudaStream_t st);
+
+// ---- multigrid pieces (Sec. 1.2) ----
+// r = b - A u (FP64), written as TR into r_out; e0_out = wd * r (optional);
+// norm_bits[b] = max(norm_bits[b], bits of max|r|) (optional).
+template <typename TR>
+cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, long long u_stride,
+                           const double* b, long long b_stride, const Coef<double>* coef,
+                           TR* r_out, TR* e0_out, const Coef<TR>* coef_r,
+                           unsigned long long* norm_bits, const int* active, Shape sh,
+                           cudaStream_t st);
+
+// Damped Jacobi: out = e + wd (r - A e).  With u64 != nullptr the result is
+// added to u64 (u64 += out) instead of being stored in out.
+template <typename T>
+cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
+                          double* u64, long long u64_stride, const Coef<T>* coef,
+                          const int* active, Shape sh, cudaStream_t st);
+
+// rr = r - A e
+template <typename T>
+cudaError_t launch_resid(int order, const Grid& g, int B, const T* e, const T* r, T* rr,
+                         const Coef<T>* coef, const int* active, Shape sh, cudaStream_t st);
+
+// e = wd * r (Jacobi from a zero initial guess); on a one-unknown grid
+// e = r / a11 (exact coarsest solve) when `exact` is set.
+template <typename T>
+cudaError_t launch_jacobi_zero(const Grid& g, int B, const T* r, T* e, const Coef<T>* coef,
+                               bool exact, const int* active, cudaStream_t st);
+
+// Full weighting: bc (coarse grid gc) <- FW(rr) (fine grid gf, N_f = 2 N_c + 1).
+template <typename T>
+cudaError_t launch_restrict(const Grid& gf, const Grid& gc, int B, const T* rr, T* bc,
+                            const int* active, cudaStream_t st);
+
+// Trilinear prolongation: uf += P ec.
+template <typename T>
+cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* ec,
+                               long long ec_stride, T* uf, long long uf_stride,
+                               const int* active, cudaStream_t st);
+
+// u64 += e
+template <typename T>
+cudaError_t launch_update(const Grid& g, int B, const T* e, double* u64, long long u64_stride,
+                          const int* active, cudaStream_t st);
+
+// max|u| per item into norm_bits (bits of the double), FP64 input.
+cudaError_t launch_maxabs(const Grid& g, int B, const double* u, long long u_stride,
+                          unsigned long long* norm_bits, const int* active, cudaStream_t st);
+
+// ---- layout and copies ----
+cudaError_t launch_dense_to_pitched(const Grid& g, int B, const double* dense, double* f,
+                                    long long f_stride, cudaStream_t st);
+cudaError_t launch_pitched_to_dense(const Grid& g, int B, const double* f, long long f_stride,
+                                    double* dense, cudaStream_t st);
+// dst_b = src_b for B items (item strides may differ, e.g. node 0 of slice p
+// from node M-1 of slice p-1).
+cudaError_t launch_copy(const Grid& g, int B, const double* src, long long src_stride,
+                        double* dst, long long dst_stride, cudaStream_t st);
+
+// ---- SDC (Sec. 1.1) ----
+// For item b with nodes U_0..U_{M-1}, F_0..F_{M-1} (node stride g.fs, item
+// stride M g.fs):
+//   J_m  = sum_j dtS[m][j] F_j + gS[m] Phi + tauS_m         (m = 0..M-2)
+//   I_m  = J_m - dtm[m] F_{m+1}      written to I (item stride (M-1) g.fs)
+//   I_0 += U_0                        (right-hand side of the first substep)
+//   residual (optional): max over m of |U_0 + sum_{m' <= m} J_{m'} - U_{m+1}|
+cudaError_t launch_integrals(int M, const Grid& g, int B, const double* U, const double* F,
+                             const double* tauS, double* I, const ItemSDC* items,
+                             const double* phi1d, unsigned long long* res_bits,
+                             const int* active, cudaStream_t st);
+
+// ---- FAS (Sec. 1.1) ----
+// Injection of the fine nodes onto the coarse level and the fine Q-integral:
+//   UG_m = UGr_m = R UF_{jm},  qF_m = R(sum_j dtQ^F[jm][j] F^F_j) + gQ^F[jm] Phi
+cudaError_t launch_fas_inject(int MF, int MG, const Grid& gf, const Grid& gg, int B,
+                              const double* UF, const double* FF, double* UG, double* UGr,
+                              double* qF, const ItemSDC* itF, const FasMap* map,
+                              const double* phig1d, cudaStream_t st);
+// tauQ_m = qF_m - sum_i dtQ^G[m][i] F^G_i - gQ^G[m] Phi;  tauS_m = tauQ_{m+1} - tauQ_m
+cudaError_t launch_fas_tau(int MG, const Grid& gg, int B, const double* qF, const double* FG,
+                           double* tauS, const ItemSDC* itG, const double* phig1d,
+                           cudaStream_t st);
+// D_j = sum_m L[j][m] (UG_m - UGr_m) on the coarse grid (MF fields per item).
+cudaError_t launch_fas_delta(int MF, int MG, const Grid& gg, int B, const double* UG,
+                             const double* UGr, double* D, const FasMap* map, cudaStream_t st);
+
+}  // namespace h3d

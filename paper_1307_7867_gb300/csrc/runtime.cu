@@ -1,0 +1,1060 @@
+// runtime.cu -- host runtime and C ABI of libheat3d.so.
+//
+// The context owns the level hierarchy (SDC levels, multigrid levels), the
+// collocation tables, per-item step data and the layout of the caller's
+// workspace.  The drivers below enqueue the kernels of mg_kernels.cu and
+// sdc_kernels.cu on the context's stream:
+//   mg_solve   -- residual refinement with V(nu1, nu2) cycles (Sec. 1.2),
+//   sweep      -- one IMEX-Euler SDC sweep (Sec. 1.1),
+//   fas_*      -- restriction / tau / interpolation between the two levels,
+//   run        -- SDC, MLSDC and PFASST over [0, T] (Sec. 1.1).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "../../include/heat3d.h"
+#include "kernels.cuh"
+#include "runtime.cuh"
+
+using namespace h3d;
+
+// ---------------------------------------------------------------------------
+// small utilities
+// ---------------------------------------------------------------------------
+
+int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->err, sizeof(c->err), fmt, ap);
+    va_end(ap);
+  }
+  return code;
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return h3d_fail(c, HEAT3D_ECUDA, "%s:%d %s: %s", __FILE__, __LINE__, #call,       \
+                      cudaGetErrorString(e_));                                          \
+  } while (0)
+
+#define RET(call)                          \
+  do {                                     \
+    int r_ = (call);                       \
+    if (r_ < 0) return r_;                 \
+  } while (0)
+
+static bool is_pow2m1(int N) { return N >= 1 && ((N + 1) & N) == 0; }
+
+// Gauss-Lobatto nodes on [0, 1] for M = 2..5: the ends and the roots of
+// P'_{M-1}, found by Newton's method on P'_{n} from Chebyshev-Lobatto guesses.
+static void lobatto_nodes(int M, double* tau) {
+  const int n = M - 1;
+  tau[0] = 0.0;
+  tau[M - 1] = 1.0;
+  for (int r = 1; r < n; ++r) {
+    double x = -cos(M_PI * r / n);
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = x;  // P_0, P_1
+      for (int k = 1; k < n; ++k) {
+        double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        p0 = p1;
+        p1 = p2;
+      }
+      // p1 = P_n, p0 = P_{n-1}
+      double dp = n * (x * p1 - p0) / (x * x - 1.0);
+      double d2p = (2.0 * x * dp - n * (n + 1) * p1) / (1.0 - x * x);
+      double dx = dp / d2p;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    tau[r] = 0.5 * (x + 1.0);
+  }
+  std::sort(tau, tau + M);
+}
+
+// Q[m][j] = int_0^{tau_m} l_j: the weights q solve the moment equations
+// sum_j q_j tau_j^p = tau_m^{p+1} / (p+1), p = 0..M-1 (Gaussian elimination).
+static void integration_matrix(int M, const double* tau, double Q[kMaxNodes][kMaxNodes]) {
+  for (int m = 0; m < M; ++m) {
+    double A[kMaxNodes][kMaxNodes + 1];
+    for (int p = 0; p < M; ++p) {
+      for (int j = 0; j < M; ++j) A[p][j] = pow(tau[j], p);
+      A[p][M] = pow(tau[m], p + 1) / (p + 1);
+    }
+    for (int col = 0; col < M; ++col) {
+      int piv = col;
+      for (int r = col + 1; r < M; ++r)
+        if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+      for (int k = 0; k <= M; ++k) std::swap(A[col][k], A[piv][k]);
+      for (int r = 0; r < M; ++r) {
+        if (r == col) continue;
+        double f = A[r][col] / A[col][col];
+        for (int k = col; k <= M; ++k) A[r][k] -= f * A[col][k];
+      }
+    }
+    for (int j = 0; j < M; ++j) Q[m][j] = (m == 0) ? 0.0 : A[j][M] / A[j][j];
+  }
+}
+
+static double kappa_of(int forcing) {
+  return forcing == HEAT3D_FORCING_EXACT ? 3.0 : 1.0;
+}
+
+// ---------------------------------------------------------------------------
+// context set-up
+// ---------------------------------------------------------------------------
+
+static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
+  if (!cfg) return h3d_fail(c, HEAT3D_EINVAL, "null config");
+  if (cfg->nlevels < 1 || cfg->nlevels > 2) return h3d_fail(c, HEAT3D_EINVAL, "nlevels must be 1 or 2");
+  for (int l = 0; l < cfg->nlevels; ++l) {
+    const heat3d_level& L = cfg->levels[l];
+    if (!is_pow2m1(L.N) || L.N > (1 << 11) - 1)
+      return h3d_fail(c, HEAT3D_EINVAL, "level %d: N=%d must be 2^k-1 (<= 2047)", l, L.N);
+    if (L.order != 2 && L.order != 4) return h3d_fail(c, HEAT3D_EINVAL, "level %d: order must be 2 or 4", l);
+    if (L.M < 2 || L.M > kMaxNodes) return h3d_fail(c, HEAT3D_EINVAL, "level %d: M must be 2..5", l);
+  }
+  if (cfg->nlevels == 2) {
+    const heat3d_level &F = cfg->levels[0], &G = cfg->levels[1];
+    if (!(F.N == G.N || F.N == 2 * G.N + 1))
+      return h3d_fail(c, HEAT3D_EINVAL, "coarse N must equal fine N or (fine N - 1)/2");
+  }
+  if (!(cfg->nu > 0) || !(cfg->dt > 0)) return h3d_fail(c, HEAT3D_EINVAL, "nu and dt must be > 0");
+  if (cfg->mg.nu1 < 1 || cfg->mg.nu2 < 0 || cfg->mg.max_cycles < 1)
+    return h3d_fail(c, HEAT3D_EINVAL, "multigrid needs nu1 >= 1, nu2 >= 0, max_cycles >= 1");
+  if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED)
+    return h3d_fail(c, HEAT3D_EINVAL, "precision must be HEAT3D_FP64 or HEAT3D_MIXED");
+  if (cfg->slices < 1 || cfg->sweeps_fine < 0 || cfg->sweeps_coarse < 0 || cfg->iters < 0)
+    return h3d_fail(c, HEAT3D_EINVAL, "slices >= 1 and non-negative sweep/iteration counts required");
+  return HEAT3D_OK;
+}
+
+static int setup_levels(heat3d_ctx* c) {
+  const heat3d_config& cfg = c->cfg;
+  int cap = std::max(std::max(cfg.batch, cfg.slices), 1);
+  for (int l = 0; l < cfg.nlevels; ++l) {
+    SdcLevel& L = c->lv[l];
+    L.L = cfg.levels[l];
+    L.B = cap;
+    L.g = make_grid(L.L.N);
+    L.nmg = 0;
+    for (int n = L.L.N;; n = (n - 1) / 2) {
+      L.mg[L.nmg] = make_grid(n);
+      L.h[L.nmg] = 1.0 / (n + 1);
+      L.nmg++;
+      if (n == 1) break;
+    }
+    lobatto_nodes(L.L.M, L.tau);
+    integration_matrix(L.L.M, L.tau, L.Q);
+    for (int m = 0; m + 1 < L.L.M; ++m)
+      for (int j = 0; j < L.L.M; ++j) L.S[m][j] = L.Q[m + 1][j] - L.Q[m][j];
+    L.items_h.assign(cap, ItemSDC{});
+    L.t0.assign(cap, 0.0);
+    L.nu.assign(cap, cfg.nu);
+    L.dt.assign(cap, cfg.dt);
+  }
+  if (cfg.nlevels == 2) {
+    SdcLevel &F = c->lv[0], &G = c->lv[1];
+    for (int m = 0; m < G.L.M; ++m) {
+      int jm = -1;
+      for (int j = 0; j < F.L.M; ++j)
+        if (fabs(F.tau[j] - G.tau[m]) < 1e-13) jm = j;
+      if (jm < 0) return h3d_fail(c, HEAT3D_EINVAL, "coarse nodes must be a subset of the fine nodes");
+      c->map.jm[m] = jm;
+    }
+    for (int j = 0; j < F.L.M; ++j)
+      for (int m = 0; m < G.L.M; ++m) {
+        double v = 1.0;
+        for (int i = 0; i < G.L.M; ++i)
+          if (i != m) v *= (F.tau[j] - G.tau[i]) / (G.tau[m] - G.tau[i]);
+        c->map.L[j][m] = v;
+      }
+  }
+  return HEAT3D_OK;
+}
+
+size_t h3d_tsize(const heat3d_ctx* c) { return c->cfg.precision == HEAT3D_MIXED ? 4 : 8; }
+
+// Lays out every device buffer in the workspace; with base == nullptr only
+// measures.  Returns the byte count.
+static size_t plan(heat3d_ctx* c, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> void* {
+    off = (off + 255) / 256 * 256;
+    void* p = base ? (void*)(base + off) : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t ts = h3d_tsize(c);
+  for (int l = 0; l < c->cfg.nlevels; ++l) {
+    SdcLevel& L = c->lv[l];
+    const int M = L.L.M, B = L.B;
+    const size_t fs = (size_t)L.g.fs * 8;
+    L.U = (double*)take(fs * B * M);
+    L.F = (double*)take(fs * B * M);
+    L.I = (double*)take(fs * B * (M - 1));
+    if (l == 1) {
+      L.tauS = (double*)take(fs * B * (M - 1));
+      L.UGr = (double*)take(fs * B * M);
+      L.qF = (double*)take(fs * B * M);
+      L.D = (double*)take(fs * B * c->lv[0].L.M);
+    }
+    L.abi_u = (double*)take(fs);
+    L.abi_b = (double*)take(fs);
+    L.abi_p0 = (double*)take(fs);
+    L.abi_p1 = (double*)take(fs);
+    for (int k = 0; k < L.nmg; ++k) {
+      size_t f = (size_t)L.mg[k].fs * ts * B;
+      L.mgb[k].b = take(f);
+      L.mgb[k].e = take(f);
+      L.mgb[k].t = take(f);
+    }
+    L.phi = (double*)take(sizeof(double) * L.L.N);
+    L.alpha_items = (double*)take(sizeof(double) * B);
+    L.alpha_nodes = (double*)take(sizeof(double) * B * M);
+    L.items_d = (ItemSDC*)take(sizeof(ItemSDC) * B);
+    L.nslots = M;  // M-1 substeps + one slot for mg_vcycle calls
+    L.coefT = take((ts == 8 ? sizeof(Coef<double>) : sizeof(Coef<float>)) * L.nslots * L.nmg * B);
+    L.coef64 = (Coef<double>*)take(sizeof(Coef<double>) * L.nslots * B);
+    L.norms = (unsigned long long*)take(sizeof(unsigned long long) * B);
+    L.active = (int*)take(sizeof(int) * B);
+  }
+  c->map_d = (FasMap*)take(sizeof(FasMap));
+  off = (off + 255) / 256 * 256;
+  return off;
+}
+
+// Per-item step data: dt S, dt Q, forcing integrals and the substep lengths.
+void h3d_fill_item(heat3d_ctx* c, int lev, int item, double t0) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  const double dt = L.dt[item], nu = L.nu[item];
+  const bool forced = c->cfg.forcing != HEAT3D_FORCING_NONE;
+  const double kap = kappa_of(c->cfg.forcing);
+  double g[kMaxNodes];
+  for (int j = 0; j < M; ++j) {
+    double t = t0 + dt * L.tau[j];
+    g[j] = forced ? -(sin(t) - kap * nu * M_PI * M_PI * cos(t)) : 0.0;
+  }
+  ItemSDC& it = L.items_h[item];
+  memset(&it, 0, sizeof(it));
+  it.nu = nu;
+  for (int m = 0; m + 1 < M; ++m) {
+    it.dtm[m] = dt * (L.tau[m + 1] - L.tau[m]);
+    double s = 0.0;
+    for (int j = 0; j < M; ++j) {
+      it.dtS[m][j] = dt * L.S[m][j];
+      s += it.dtS[m][j] * g[j];
+    }
+    it.gS[m] = s;
+  }
+  for (int m = 0; m < M; ++m) {
+    double s = 0.0;
+    for (int j = 0; j < M; ++j) {
+      it.dtQ[m][j] = dt * L.Q[m][j];
+      s += it.dtQ[m][j] * g[j];
+    }
+    it.gQ[m] = s;
+  }
+  L.t0[item] = t0;
+}
+
+int h3d_upload_items(heat3d_ctx* c, int lev, int b0, int B) {
+  SdcLevel& L = c->lv[lev];
+  CK(cudaMemcpyAsync(L.items_d + b0, L.items_h.data() + b0, sizeof(ItemSDC) * B,
+                     cudaMemcpyHostToDevice, c->st));
+  return HEAT3D_OK;
+}
+
+// Multigrid coefficients of A = I - c Delta_h on every level, for slot `slot`
+// of items [b0, b0 + B) with per-item c values.
+int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* cvals) {
+  SdcLevel& L = c->lv[lev];
+  const int order = L.L.order;
+  const bool f32 = h3d_tsize(c) == 4;
+  std::vector<Coef<double>> c64(B);
+  std::vector<Coef<double>> cd((size_t)L.nmg * B);
+  for (int k = 0; k < L.nmg; ++k) {
+    const double h = L.h[k];
+    for (int b = 0; b < B; ++b) {
+      const double cc = cvals[b];
+      Coef<double> q;
+      if (order == 2) {
+        q.e = cc / (h * h);
+        q.d = 1.0 + 6.0 * q.e;
+        q.wd = (6.0 / 7.0) / q.d;
+        q.a11 = 1.0 + 6.0 * q.e;
+      } else {
+        q.e = cc / (12.0 * h * h);
+        q.d = 1.0 + 90.0 * q.e;
+        q.wd = (9.0 / 11.0) / q.d;
+        q.a11 = 1.0 + 84.0 * q.e;
+      }
+      cd[(size_t)k * B + b] = q;
+      if (k == 0) c64[b] = q;
+    }
+  }
+  CK(cudaMemcpyAsync(L.coef64 + (size_t)slot * L.B + b0, c64.data(), sizeof(Coef<double>) * B,
+                     cudaMemcpyHostToDevice, c->st));
+  for (int k = 0; k < L.nmg; ++k) {
+    size_t base = ((size_t)slot * L.nmg + k) * L.B + b0;
+    if (f32) {
+      std::vector<Coef<float>> cf(B);
+      for (int b = 0; b < B; ++b) {
+        const Coef<double>& q = cd[(size_t)k * B + b];
+        cf[b] = Coef<float>{(float)q.d, (float)q.e, (float)q.wd, (float)q.a11};
+      }
+      CK(cudaMemcpyAsync((Coef<float>*)L.coefT + base, cf.data(), sizeof(Coef<float>) * B,
+                         cudaMemcpyHostToDevice, c->st));
+    } else {
+      CK(cudaMemcpyAsync((Coef<double>*)L.coefT + base, cd.data() + (size_t)k * B,
+                         sizeof(Coef<double>) * B, cudaMemcpyHostToDevice, c->st));
+    }
+  }
+  return HEAT3D_OK;
+}
+
+// Substep coefficients c = dt_m nu of items [b0, b0+B) for every substep slot,
+// plus alpha = nu / h^2 (or nu / (12 h^2)) for the operator kernels.
+int h3d_set_item_operators(heat3d_ctx* c, int lev, int b0, int B) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  std::vector<double> cv(B);
+  for (int m = 0; m + 1 < M; ++m) {
+    for (int b = 0; b < B; ++b) cv[b] = L.dt[b0 + b] * (L.tau[m + 1] - L.tau[m]) * L.nu[b0 + b];
+    RET(h3d_set_coefs(c, lev, m, b0, B, cv.data()));
+  }
+  const double h = L.h[0];
+  std::vector<double> ai(B), an((size_t)B * M);
+  for (int b = 0; b < B; ++b) {
+    double nu = L.nu[b0 + b];
+    ai[b] = L.L.order == 2 ? nu / (h * h) : nu / (12.0 * h * h);
+    for (int m = 0; m < M; ++m) an[(size_t)b * M + m] = ai[b];
+  }
+  CK(cudaMemcpyAsync(L.alpha_items + b0, ai.data(), sizeof(double) * B, cudaMemcpyHostToDevice, c->st));
+  CK(cudaMemcpyAsync(L.alpha_nodes + (size_t)b0 * M, an.data(), sizeof(double) * B * M,
+                     cudaMemcpyHostToDevice, c->st));
+  return HEAT3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// multigrid (Sec. 1.2): residual refinement with V-cycles on the error
+// ---------------------------------------------------------------------------
+
+template <typename T>
+static T* mgbuf(SdcLevel& L, int k, int which, int b0) {
+  void* p = which == 0 ? L.mgb[k].b : which == 1 ? L.mgb[k].e : L.mgb[k].t;
+  return (T*)p + (size_t)b0 * L.mg[k].fs;
+}
+
+template <typename T>
+static const Coef<T>* coefT(SdcLevel& L, int slot, int k, int b0) {
+  return (const Coef<T>*)L.coefT + ((size_t)slot * L.nmg + k) * L.B + b0;
+}
+
+// One V(nu1, nu2) cycle on level k for the error equation A e = b_k.  On the
+// finest level the first smoothing result e_0 = wd * r was written by the
+// residual kernel and the last post-smoothing sweep adds its result to u64.
+// Returns the buffer holding the level's correction (nullptr on level 0).
+template <typename T>
+static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int B,
+                        const int* act, double* u64, long long us, T** result) {
+  const Grid& g = L.mg[k];
+  const int order = L.L.order;
+  const int nu1 = c->cfg.mg.nu1, nu2 = c->cfg.mg.nu2;
+  cudaStream_t st = c->st;
+  T* b = mgbuf<T>(L, k, 0, b0);
+  T* e = mgbuf<T>(L, k, 1, b0);
+  T* t = mgbuf<T>(L, k, 2, b0);
+  const Coef<T>* cf = coefT<T>(L, slot, k, b0);
+  const size_t ts = sizeof(T), pts = (size_t)g.N * g.N * g.N * B;
+  if (g.N == 1) {
+    CK(launch_jacobi_zero<T>(g, B, b, e, cf, true, act, st));
+    if (k == 0) {
+      CK(launch_update<T>(g, B, e, u64, us, act, st));
+      *result = nullptr;
+    } else {
+      *result = e;
+    }
+    return HEAT3D_OK;
+  }
+  if (k > 0) {
+    CK(launch_jacobi_zero<T>(g, B, b, e, cf, false, act, st));
+    c->bytes += 2.0 * ts * pts;
+  }
+  T* cur = e;
+  T* oth = t;
+  for (int s = 1; s < nu1; ++s) {
+    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    c->bytes += 3.0 * ts * pts;
+    std::swap(cur, oth);
+  }
+  CK(launch_resid<T>(order, g, B, cur, b, oth, cf, act, c->shape, st));
+  CK(launch_restrict<T>(g, L.mg[k + 1], B, oth, mgbuf<T>(L, k + 1, 0, b0), act, st));
+  c->bytes += 3.0 * ts * pts + ts * pts * (1.0 + 1.0 / 8.0);
+  T* ce = nullptr;
+  RET(vcycle_level<T>(c, L, slot, k + 1, b0, B, act, u64, us, &ce));
+  CK(launch_prolong_add<T>(L.mg[k + 1], g, B, ce, L.mg[k + 1].fs, cur, g.fs, act, st));
+  c->bytes += ts * pts * (2.0 + 1.0 / 8.0);
+  for (int s = 0; s < nu2; ++s) {
+    if (k == 0 && s == nu2 - 1) {
+      CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, c->shape, st));
+      c->bytes += (2.0 * ts + 16.0) * pts;
+      *result = nullptr;
+      return HEAT3D_OK;
+    }
+    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    c->bytes += 3.0 * ts * pts;
+    std::swap(cur, oth);
+  }
+  if (k == 0) {
+    CK(launch_update<T>(g, B, cur, u64, us, act, st));
+    c->bytes += (ts + 16.0) * pts;
+    *result = nullptr;
+  } else {
+    *result = cur;
+  }
+  return HEAT3D_OK;
+}
+
+static int read_norms(heat3d_ctx* c, SdcLevel& L, int b0, int B, std::vector<double>& out) {
+  std::vector<unsigned long long> h(B);
+  CK(cudaMemcpyAsync(h.data(), L.norms + b0, sizeof(unsigned long long) * B,
+                     cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  out.resize(B);
+  for (int b = 0; b < B; ++b) {
+    unsigned long long v = h[b];
+    double d;
+    memcpy(&d, &v, 8);
+    out[b] = d;  // NaN/Inf keep their bit patterns
+  }
+  return HEAT3D_OK;
+}
+
+// Solve (I - c_b Delta_h) u_b = rhs_b for items [b0, b0 + B) of level lev, u
+// warm-started and updated in place (item strides us, bs).  Coefficients of
+// slot `slot` must be set.  Returns ENOTCONV / ENAN per the tolerance rule.
+template <typename T>
+static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
+                      const double* rhs, long long bs, int max_cycles, double tol,
+                      heat3d_stats* s) {
+  SdcLevel& L = c->lv[lev];
+  const Grid& g = L.mg[0];
+  const int order = L.L.order;
+  cudaStream_t st = c->st;
+  int* act = L.active + b0;
+  std::vector<int> ha(B, 1);
+  CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  T* r = mgbuf<T>(L, 0, 0, b0);
+  T* e0 = mgbuf<T>(L, 0, 1, b0);
+  const Coef<T>* cf = coefT<T>(L, slot, 0, b0);
+  const Coef<double>* c64 = L.coef64 + (size_t)slot * L.B + b0;
+  const double pts = (double)g.N * g.N * g.N * B;
+  const bool fixed = tol < 0;
+  std::vector<double> nrm;
+  auto residual = [&]() -> int {
+    CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
+    CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, c->shape, st));
+    c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
+    return HEAT3D_OK;
+  };
+  RET(residual());
+  int cycles = 0, live = B;
+  if (!fixed) {
+    RET(read_norms(c, L, b0, B, nrm));
+    for (int b = 0; b < B; ++b) {
+      if (!(nrm[b] <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
+      if (nrm[b] <= tol) { ha[b] = 0; --live; }
+    }
+    if (live < B) CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  }
+  while (cycles < max_cycles && live > 0) {
+    T* dummy = nullptr;
+    RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &dummy));
+    ++cycles;
+    if (s) s->vcycles += live;
+    RET(residual());
+    if (!fixed) {
+      RET(read_norms(c, L, b0, B, nrm));
+      bool changed = false;
+      for (int b = 0; b < B; ++b) {
+        if (!ha[b]) continue;
+        if (!(nrm[b] <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
+        if (nrm[b] <= tol) { ha[b] = 0; --live; changed = true; }
+      }
+      if (changed && live > 0)
+        CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
+    }
+  }
+  if (s) s->solves += B;
+  if (fixed) {
+    if (s) {
+      RET(read_norms(c, L, b0, B, nrm));
+      double mx = 0;
+      for (double v : nrm) mx = std::max(mx, v);
+      s->mg_residual = mx;
+    }
+    return HEAT3D_OK;
+  }
+  double mx = 0;
+  for (int b = 0; b < B; ++b) mx = std::max(mx, nrm[b]);
+  if (s) s->mg_residual = mx;
+  if (live > 0) {
+    if (s) s->notconv += live;
+    return h3d_fail(c, HEAT3D_ENOTCONV, "multigrid: %d item(s) above tol %.3g after %d cycles", live,
+                    tol, max_cycles);
+  }
+  return HEAT3D_OK;
+}
+
+int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
+                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s) {
+  if (h3d_tsize(c) == 4) return mg_solve_T<float>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, s);
+  return mg_solve_T<double>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, s);
+}
+
+// ---------------------------------------------------------------------------
+// SDC (Sec. 1.1)
+// ---------------------------------------------------------------------------
+
+// F at every node of items [b0, b0+B) from U.
+int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  const long long fs = L.g.fs;
+  CK(launch_lap(L.L.order, L.g, B * M, L.U + (size_t)b0 * M * fs, fs, L.F + (size_t)b0 * M * fs, fs,
+                L.alpha_nodes + (size_t)b0 * M, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+  c->bytes += 16.0 * L.L.N * L.L.N * (double)L.L.N * B * M;
+  return HEAT3D_OK;
+}
+
+// Collocation residual of items [b0, b0+B): max over items into *res (and per
+// item into per_item when given).  Synchronises.
+int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector<double>* per_item) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  const long long fs = L.g.fs;
+  CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, c->st));
+  CK(launch_integrals(M, L.g, B, L.U + (size_t)b0 * M * fs, L.F + (size_t)b0 * M * fs,
+                      (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
+                      nullptr, L.items_d + b0, L.phi, L.norms + b0, nullptr, c->st));
+  std::vector<double> n;
+  RET(read_norms(c, L, b0, B, n));
+  double mx = 0;
+  for (double v : n) {
+    if (!(v <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf in the collocation residual");
+    mx = std::max(mx, v);
+  }
+  if (res) *res = mx;
+  if (per_item) *per_item = n;
+  return HEAT3D_OK;
+}
+
+// One sweep over items [b0, b0+B).  When check_tol >= 0 the residual of the
+// incoming iterate is computed by the quadrature kernel first; if it is
+// <= check_tol for every item the sweep is skipped and 1 is returned.
+int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_stats* s) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  const long long fs = L.g.fs;
+  const double pts = (double)L.L.N * L.L.N * L.L.N * B;
+  cudaStream_t st = c->st;
+  double* U = L.U + (size_t)b0 * M * fs;
+  double* F = L.F + (size_t)b0 * M * fs;
+  double* I = L.I + (size_t)b0 * (M - 1) * fs;
+  const bool want = check_tol >= 0;
+  if (want) CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
+  CK(launch_integrals(M, L.g, B, U, F, (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
+                      I, L.items_d + b0, L.phi, want ? L.norms + b0 : nullptr, nullptr, st));
+  c->bytes += 8.0 * pts * (2 * M + (M - 1) + ((lev == 1 && L.has_tau) ? (M - 1) : 0));
+  if (want) {
+    std::vector<double> n;
+    RET(read_norms(c, L, b0, B, n));
+    double mx = 0;
+    for (double v : n) {
+      if (!(v <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf in the collocation residual");
+      mx = std::max(mx, v);
+    }
+    if (s) s->residual = mx;
+    if (mx <= check_tol) return 1;
+  }
+  int status = HEAT3D_OK;
+  for (int m = 0; m + 1 < M; ++m) {
+    int rc = h3d_mg_solve(c, lev, m, b0, B, U + (size_t)(m + 1) * fs, (long long)M * fs,
+                          I + (size_t)m * fs, (long long)(M - 1) * fs, c->cfg.mg.max_cycles,
+                          c->cfg.mg.tol, s);
+    if (rc == HEAT3D_ENOTCONV) status = rc;
+    else if (rc < 0) return rc;
+    const bool add = m + 1 <= M - 2;
+    CK(launch_lap(L.L.order, L.g, B, U + (size_t)(m + 1) * fs, (long long)M * fs,
+                  F + (size_t)(m + 1) * fs, (long long)M * fs, L.alpha_items + b0,
+                  add ? I + (size_t)(m + 1) * fs : nullptr, add ? I + (size_t)(m + 1) * fs : nullptr,
+                  (long long)(M - 1) * fs, nullptr, c->shape, st));
+    c->bytes += pts * (16.0 + (add ? 16.0 : 0.0));
+  }
+  if (s) s->sweeps += 1;
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// FAS between level 0 (fine) and level 1 (coarse)
+// ---------------------------------------------------------------------------
+
+int h3d_fas_restrict(heat3d_ctx* c, int b0, int B) {
+  SdcLevel &F = c->lv[0], &G = c->lv[1];
+  const int MF = F.L.M, MG = G.L.M;
+  const long long ff = F.g.fs, gf = G.g.fs;
+  cudaStream_t st = c->st;
+  CK(launch_fas_inject(MF, MG, F.g, G.g, B, F.U + (size_t)b0 * MF * ff, F.F + (size_t)b0 * MF * ff,
+                       G.U + (size_t)b0 * MG * gf, G.UGr + (size_t)b0 * MG * gf,
+                       G.qF + (size_t)b0 * MG * gf, F.items_d + b0, c->map_d, F.phi, st));
+  CK(launch_lap(G.L.order, G.g, B * MG, G.U + (size_t)b0 * MG * gf, gf, G.F + (size_t)b0 * MG * gf, gf,
+                G.alpha_nodes + (size_t)b0 * MG, nullptr, nullptr, 0, nullptr, c->shape, st));
+  CK(launch_fas_tau(MG, G.g, B, G.qF + (size_t)b0 * MG * gf, G.F + (size_t)b0 * MG * gf,
+                    G.tauS + (size_t)b0 * (MG - 1) * gf, G.items_d + b0, G.phi, st));
+  G.has_tau = true;
+  const double pg = (double)G.L.N * G.L.N * G.L.N * B;
+  c->bytes += pg * 8.0 * (2 * MF + 3 * MG) + pg * 16.0 * MG + pg * 8.0 * (2 * MG + MG - 1);
+  return HEAT3D_OK;
+}
+
+int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
+  SdcLevel &F = c->lv[0], &G = c->lv[1];
+  const int MF = F.L.M, MG = G.L.M;
+  const long long ff = F.g.fs, gf = G.g.fs;
+  cudaStream_t st = c->st;
+  double* D = G.D + (size_t)b0 * MF * gf;
+  CK(launch_fas_delta(MF, MG, G.g, B, G.U + (size_t)b0 * MG * gf, G.UGr + (size_t)b0 * MG * gf, D,
+                      c->map_d, st));
+  if (F.L.N == G.L.N) {
+    CK(launch_update<double>(F.g, B * MF, D, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
+  } else {
+    CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
+  }
+  RET(h3d_eval_F(c, 0, b0, B));
+  const double pf = (double)F.L.N * F.L.N * F.L.N * B;
+  c->bytes += pf * MF * 16.0 + pf / 8.0 * 8.0 * (2 * MG + MF);
+  return HEAT3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// drivers over [0, T]
+// ---------------------------------------------------------------------------
+
+// Spread the pitched field u (one item) to every node of items [b0, b0+B).
+int h3d_spread(heat3d_ctx* c, int lev, int b0, int B, const double* u) {
+  SdcLevel& L = c->lv[lev];
+  const int M = L.L.M;
+  const long long fs = L.g.fs;
+  CK(launch_copy(L.g, B * M, u, 0, L.U + (size_t)b0 * M * fs, fs, c->st));
+  RET(h3d_eval_F(c, lev, b0, B));
+  c->bytes += 8.0 * L.L.N * L.L.N * (double)L.L.N * B * M;
+  return HEAT3D_OK;
+}
+
+// Serial coarse pass over slices 0..P-1: slice p > 0 starts from the coarse
+// end value of slice p-1.
+static int coarse_pass(heat3d_ctx* c, int P, heat3d_stats* s) {
+  SdcLevel& G = c->lv[1];
+  const int MG = G.L.M;
+  const long long gf = G.g.fs;
+  int status = HEAT3D_OK;
+  for (int p = 0; p < P; ++p) {
+    if (p > 0) {
+      CK(launch_copy(G.g, 1, G.U + ((size_t)(p - 1) * MG + MG - 1) * gf, 0, G.U + (size_t)p * MG * gf, 0, c->st));
+      CK(launch_lap(G.L.order, G.g, 1, G.U + (size_t)p * MG * gf, 0, G.F + (size_t)p * MG * gf, 0,
+                    G.alpha_items + p, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+    }
+    for (int k = 0; k < c->cfg.sweeps_coarse; ++k) {
+      int rc = h3d_sweep(c, 1, p, 1, -1.0, s);
+      if (rc == HEAT3D_ENOTCONV) status = rc;
+      else if (rc < 0) return rc;
+    }
+  }
+  return status;
+}
+
+// Fine end value of slice p-1 becomes node 0 of slice p (p = 1..P-1).
+static int forward_fine(heat3d_ctx* c, int P) {
+  if (P < 2) return HEAT3D_OK;
+  SdcLevel& F = c->lv[0];
+  const int MF = F.L.M;
+  const long long ff = F.g.fs;
+  CK(launch_copy(F.g, P - 1, F.U + (size_t)(MF - 1) * ff, (long long)MF * ff, F.U + (size_t)MF * ff,
+                 (long long)MF * ff, c->st));
+  CK(launch_lap(F.L.order, F.g, P - 1, F.U + (size_t)MF * ff, (long long)MF * ff, F.F + (size_t)MF * ff,
+                (long long)MF * ff, F.alpha_items + 1, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+  return HEAT3D_OK;
+}
+
+int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
+  const heat3d_config& cfg = c->cfg;
+  SdcLevel& F = c->lv[0];
+  const int P = cfg.nlevels == 2 ? cfg.slices : 1;
+  const int nsteps = (int)llround(cfg.T / cfg.dt);
+  if (fabs(nsteps * cfg.dt - cfg.T) > 1e-9 * std::max(1.0, cfg.T))
+    return h3d_fail(c, HEAT3D_EINVAL, "T must be a multiple of dt");
+  if (nsteps % P != 0) return h3d_fail(c, HEAT3D_EINVAL, "number of steps must be a multiple of slices");
+  if (P > F.B) return h3d_fail(c, HEAT3D_EINVAL, "slices exceed the batch capacity");
+  const int MF = F.L.M;
+  const long long ff = F.g.fs;
+  int status = HEAT3D_OK;
+  for (int l = 0; l < cfg.nlevels; ++l) {
+    for (int p = 0; p < P; ++p) {
+      c->lv[l].nu[p] = cfg.nu;
+      c->lv[l].dt[p] = cfg.dt;
+    }
+    RET(h3d_set_item_operators(c, l, 0, P));
+  }
+  for (int blk = 0; blk < nsteps / P; ++blk) {
+    const double tb = (double)blk * P * cfg.dt;
+    for (int l = 0; l < cfg.nlevels; ++l) {
+      for (int p = 0; p < P; ++p) h3d_fill_item(c, l, p, tb + p * cfg.dt);
+      RET(h3d_upload_items(c, l, 0, P));
+    }
+    RET(h3d_spread(c, 0, 0, P, ucur));
+    if (cfg.nlevels == 1) {
+      for (int k = 0; k < cfg.sweeps_fine; ++k) {
+        int rc = h3d_sweep(c, 0, 0, 1, cfg.tol_sdc >= 0 ? cfg.tol_sdc : -1.0, s);
+        if (rc == 1) break;
+        if (rc == HEAT3D_ENOTCONV) status = rc;
+        else if (rc < 0) return rc;
+      }
+    } else {
+      c->lv[1].has_tau = false;
+      if (cfg.predictor) {
+        RET(h3d_fas_restrict(c, 0, P));
+        int rc = coarse_pass(c, P, s);
+        if (rc == HEAT3D_ENOTCONV) status = rc;
+        else if (rc < 0) return rc;
+        RET(h3d_fas_interpolate(c, 0, P));
+        RET(forward_fine(c, P));
+      }
+      for (int it = 0; it < cfg.iters; ++it) {
+        bool done = false;
+        for (int k = 0; k < cfg.sweeps_fine; ++k) {
+          double chk = (k == 0 && it > 0 && cfg.tol_sdc >= 0) ? cfg.tol_sdc : -1.0;
+          int rc = h3d_sweep(c, 0, 0, P, chk, s);
+          if (rc == 1) { done = true; break; }
+          if (rc == HEAT3D_ENOTCONV) status = rc;
+          else if (rc < 0) return rc;
+        }
+        if (done) break;
+        RET(h3d_fas_restrict(c, 0, P));
+        int rc = coarse_pass(c, P, s);
+        if (rc == HEAT3D_ENOTCONV) status = rc;
+        else if (rc < 0) return rc;
+        RET(h3d_fas_interpolate(c, 0, P));
+        RET(forward_fine(c, P));
+        if (s) s->iters += 1;
+      }
+    }
+    if (s) {
+      double r = 0;
+      RET(h3d_residual(c, 0, 0, P, &r, nullptr));
+      s->residual = r;
+      s->steps += P;
+    }
+    CK(launch_copy(F.g, 1, F.U + ((size_t)(P - 1) * MF + MF - 1) * ff, 0, ucur, 0, c->st));
+  }
+  return status;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// dense host-or-device N^3 array -> pitched field (one item) via abi_b staging.
+int h3d_load_dense(heat3d_ctx* c, int lev, const double* src, double* dst_pitched) {
+  SdcLevel& L = c->lv[lev];
+  const size_t n = (size_t)L.L.N * L.L.N * L.L.N;
+  const double* dsrc = src;
+  if (!is_device_ptr(src)) {
+    CK(cudaMemcpyAsync(L.abi_b, src, n * 8, cudaMemcpyHostToDevice, c->st));
+    dsrc = L.abi_b;
+  }
+  CK(launch_dense_to_pitched(L.g, 1, dsrc, dst_pitched, 0, c->st));
+  return HEAT3D_OK;
+}
+
+int h3d_store_dense(heat3d_ctx* c, int lev, const double* src_pitched, double* dst) {
+  SdcLevel& L = c->lv[lev];
+  const size_t n = (size_t)L.L.N * L.L.N * L.L.N;
+  if (is_device_ptr(dst)) {
+    CK(launch_pitched_to_dense(L.g, 1, src_pitched, 0, dst, c->st));
+    return HEAT3D_OK;
+  }
+  CK(launch_pitched_to_dense(L.g, 1, src_pitched, 0, L.abi_b, c->st));
+  CK(cudaMemcpyAsync(dst, L.abi_b, n * 8, cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+#define NEED_BOUND(c)                                                                  \
+  do {                                                                                 \
+    if (!(c)) return HEAT3D_EINVAL;                                                    \
+    if (!(c)->bound) return h3d_fail((c), HEAT3D_ESTATE, "no workspace bound");        \
+  } while (0)
+
+extern "C" {
+
+void heat3d_config_default(heat3d_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->nu = 0.1;
+  cfg->T = 1.0;
+  cfg->dt = 1.0 / 64;
+  cfg->nlevels = 2;
+  cfg->levels[0] = heat3d_level{31, 4, 5};
+  cfg->levels[1] = heat3d_level{15, 2, 3};
+  cfg->sweeps_fine = 2;
+  cfg->sweeps_coarse = 1;
+  cfg->slices = 1;
+  cfg->iters = 20;
+  cfg->tol_sdc = 1e-10;
+  cfg->predictor = 1;
+  cfg->mg = heat3d_mg{2, 1, 50, 1e-10};
+  cfg->precision = HEAT3D_FP64;
+  cfg->forcing = HEAT3D_FORCING_PAPER_LITERAL;
+  cfg->batch = 1;
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->use_graphs = 0;
+}
+
+int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes) {
+  if (!cfg || !bytes) return HEAT3D_EINVAL;
+  heat3d_ctx tmp;
+  int rc = validate(&tmp, cfg);
+  if (rc < 0) return rc;
+  tmp.cfg = *cfg;
+  rc = setup_levels(&tmp);
+  if (rc < 0) return rc;
+  *bytes = plan(&tmp, nullptr);
+  return HEAT3D_OK;
+}
+
+int heat3d_init(const heat3d_config* cfg, heat3d_ctx** out) {
+  if (!out) return HEAT3D_EINVAL;
+  *out = nullptr;
+  heat3d_ctx* c = new heat3d_ctx();
+  int rc = validate(c, cfg);
+  if (rc < 0) { delete c; return rc; }
+  c->cfg = *cfg;
+  c->st = (cudaStream_t)cfg->stream;
+  rc = setup_levels(c);
+  if (rc < 0) { delete c; return rc; }
+  c->ws_need = plan(c, nullptr);
+  *out = c;
+  return HEAT3D_OK;
+}
+
+int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
+  if (!c || !dptr) return HEAT3D_EINVAL;
+  if (bytes < c->ws_need) return h3d_fail(c, HEAT3D_ENOMEM, "workspace %zu < %zu bytes", bytes, c->ws_need);
+  if (((uintptr_t)dptr) % 256) return h3d_fail(c, HEAT3D_EINVAL, "workspace must be 256-byte aligned");
+  CK(cudaSetDevice(c->cfg.device));
+  plan(c, (char*)dptr);
+  c->ws = dptr;
+  c->ws_bytes = bytes;
+  CK(cudaMemsetAsync(dptr, 0, c->ws_need, c->st));
+  CK(cudaMemcpyAsync(c->map_d, &c->map, sizeof(FasMap), cudaMemcpyHostToDevice, c->st));
+  for (int l = 0; l < c->cfg.nlevels; ++l) {
+    SdcLevel& L = c->lv[l];
+    std::vector<double> phi(L.L.N);
+    for (int i = 0; i < L.L.N; ++i) phi[i] = sin(M_PI * (i + 1) * L.h[0]);
+    CK(cudaMemcpyAsync(L.phi, phi.data(), sizeof(double) * L.L.N, cudaMemcpyHostToDevice, c->st));
+    RET(h3d_set_item_operators(c, l, 0, L.B));
+    for (int b = 0; b < L.B; ++b) h3d_fill_item(c, l, b, 0.0);
+    RET(h3d_upload_items(c, l, 0, L.B));
+  }
+  CK(cudaStreamSynchronize(c->st));
+  c->bound = true;
+  return HEAT3D_OK;
+}
+
+int heat3d_destroy(heat3d_ctx* c) {
+  if (!c) return HEAT3D_EINVAL;
+  h3d_destroy_extras(c);
+  delete c;
+  return HEAT3D_OK;
+}
+
+const char* heat3d_last_error(const heat3d_ctx* c) { return c ? c->err : "null context"; }
+
+int heat3d_set_stream(heat3d_ctx* c, void* stream) {
+  if (!c) return HEAT3D_EINVAL;
+  c->st = (cudaStream_t)stream;
+  return HEAT3D_OK;
+}
+
+int heat3d_apply_laplacian(heat3d_ctx* c, int level, const double* u, double* out) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || !u || !out) return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  SdcLevel& L = c->lv[level];
+  RET(h3d_load_dense(c, level, u, L.abi_u));
+  CK(launch_lap(L.L.order, L.g, 1, L.abi_u, 0, L.abi_p0, 0, L.alpha_items, nullptr, nullptr, 0,
+                nullptr, c->shape, c->st));
+  RET(h3d_store_dense(c, level, L.abi_p0, out));
+  return HEAT3D_OK;
+}
+
+int mg_vcycle(heat3d_ctx* c, int level, double cc, const double* rhs, double* u, int max_cycles,
+              double tol, heat3d_stats* stats) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || !rhs || !u || max_cycles < 0 || !(cc >= 0))
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  SdcLevel& L = c->lv[level];
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->st));
+  double* ub = L.abi_p0;  // pitched solution
+  double* bb = L.abi_p1;  // pitched right-hand side
+  RET(h3d_load_dense(c, level, rhs, bb));
+  RET(h3d_load_dense(c, level, u, ub));
+  const int slot = L.nslots - 1;
+  RET(h3d_set_coefs(c, level, slot, 0, 1, &cc));
+  heat3d_stats loc{};
+  c->bytes = 0;
+  int rc = max_cycles > 0 ? h3d_mg_solve(c, level, slot, 0, 1, ub, 0, bb, 0, max_cycles, tol, &loc)
+                          : HEAT3D_OK;
+  if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
+  RET(h3d_store_dense(c, level, ub, u));
+  CK(cudaEventRecord(e1, c->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  loc.seconds = ms * 1e-3;
+  loc.bytes = c->bytes;
+  if (stats) *stats = loc;
+  return rc;
+}
+
+int heat3d_set_state(heat3d_ctx* c, int level, int item, double t0, const double* u0) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || item < 0 || item >= c->lv[level].B || !u0)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  SdcLevel& L = c->lv[level];
+  RET(h3d_load_dense(c, level, u0, L.abi_u));
+  RET(h3d_spread(c, level, item, 1, L.abi_u));
+  h3d_fill_item(c, level, item, t0);
+  RET(h3d_upload_items(c, level, item, 1));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+int heat3d_get_node(heat3d_ctx* c, int level, int item, int node, double* out) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || item < 0 || item >= c->lv[level].B || node < 0 ||
+      node >= c->lv[level].L.M || !out)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  SdcLevel& L = c->lv[level];
+  RET(h3d_store_dense(c, level, L.U + ((size_t)item * L.L.M + node) * L.g.fs, out));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+int heat3d_set_node(heat3d_ctx* c, int level, int item, int node, const double* in) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || item < 0 || item >= c->lv[level].B || node < 0 ||
+      node >= c->lv[level].L.M || !in)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  SdcLevel& L = c->lv[level];
+  double* dst = L.U + ((size_t)item * L.L.M + node) * L.g.fs;
+  RET(h3d_load_dense(c, level, in, dst));
+  CK(launch_lap(L.L.order, L.g, 1, dst, 0, L.F + ((size_t)item * L.L.M + node) * L.g.fs, 0,
+                L.alpha_items + item, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+int sdc_sweep(heat3d_ctx* c, int level, int batch_begin, int batch_count, heat3d_stats* stats) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || batch_begin < 0 || batch_count < 1 ||
+      batch_begin + batch_count > c->lv[level].B)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  heat3d_stats loc{};
+  c->bytes = 0;
+  int rc = h3d_sweep(c, level, batch_begin, batch_count, -1.0, &loc);
+  CK(cudaStreamSynchronize(c->st));
+  loc.bytes = c->bytes;
+  if (stats) *stats = loc;
+  return rc;
+}
+
+int heat3d_sdc_residual(heat3d_ctx* c, int level, int item, double* residual) {
+  NEED_BOUND(c);
+  if (level < 0 || level >= c->cfg.nlevels || item < 0 || item >= c->lv[level].B || !residual)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  return h3d_residual(c, level, item, 1, residual, nullptr);
+}
+
+int heat3d_fas_restrict(heat3d_ctx* c, int begin, int count) {
+  NEED_BOUND(c);
+  if (c->cfg.nlevels != 2 || begin < 0 || count < 1 || begin + count > c->lv[0].B)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  RET(h3d_fas_restrict(c, begin, count));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+int heat3d_fas_interpolate(heat3d_ctx* c, int begin, int count) {
+  NEED_BOUND(c);
+  if (c->cfg.nlevels != 2 || begin < 0 || count < 1 || begin + count > c->lv[0].B)
+    return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
+  RET(h3d_fas_interpolate(c, begin, count));
+  CK(cudaStreamSynchronize(c->st));
+  return HEAT3D_OK;
+}
+
+int pfasst_run(heat3d_ctx* c, const double* u0, double* uT, heat3d_stats* stats) {
+  NEED_BOUND(c);
+  if (!u0 || !uT) return h3d_fail(c, HEAT3D_EINVAL, "null u0/uT");
+  SdcLevel& F = c->lv[0];
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, c->st));
+  heat3d_stats loc{};
+  c->bytes = 0;
+  RET(h3d_load_dense(c, 0, u0, F.abi_u));
+  int rc = h3d_run(c, F.abi_u, &loc);
+  if (rc < 0 && rc != HEAT3D_ENOTCONV) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+  }
+  RET(h3d_store_dense(c, 0, F.abi_u, uT));
+  CK(cudaEventRecord(e1, c->st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  loc.seconds = ms * 1e-3;
+  loc.bytes = c->bytes;
+  if (stats) *stats = loc;
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// runtime.cuh -- the context structure and the host drivers shared by the
+// runtime (runtime.cu), the CUDA-graph layer and the serving loop.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/heat3d.h"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace h3d {
+
+struct MgBufs {
+  void* b = nullptr;  // right-hand side of the level's error equation (level 0: the residual)
+  void* e = nullptr;  // correction
+  void* t = nullptr;  // ping-pong partner of e
+};
+
+// One SDC level of the hierarchy with its multigrid levels and its items
+// (PFASST slices or independent problems), all of the same grid.
+struct SdcLevel {
+  heat3d_level L{};
+  int B = 0;  // item capacity
+  Grid g{};
+  int nmg = 0;
+  Grid mg[kMaxLevels]{};
+  double h[kMaxLevels]{};
+  double tau[kMaxNodes]{}, Q[kMaxNodes][kMaxNodes]{}, S[kMaxNodes - 1][kMaxNodes]{};
+  // device buffers (workspace); node fields are [item][node] at stride g.fs
+  double *U = nullptr, *F = nullptr, *I = nullptr;
+  double *tauS = nullptr, *UGr = nullptr, *qF = nullptr, *D = nullptr;  // coarse level only
+  double *abi_u = nullptr, *abi_b = nullptr, *abi_p0 = nullptr, *abi_p1 = nullptr;
+  MgBufs mgb[kMaxLevels];
+  double* phi = nullptr;  // sin(pi x_i), i = 1..N
+  double* alpha_items = nullptr;
+  double* alpha_nodes = nullptr;
+  ItemSDC* items_d = nullptr;
+  int nslots = 0;
+  void* coefT = nullptr;  // Coef<T>[slot][mg level][item]
+  Coef<double>* coef64 = nullptr;  // Coef<double>[slot][item], finest multigrid level
+  unsigned long long* norms = nullptr;
+  int* active = nullptr;
+  // host mirrors
+  std::vector<ItemSDC> items_h;
+  std::vector<double> t0, nu, dt;
+  bool has_tau = false;
+};
+
+}  // namespace h3d
+
+struct heat3d_ctx {
+  heat3d_config cfg{};
+  h3d::SdcLevel lv[2];
+  h3d::FasMap map{};
+  h3d::FasMap* map_d = nullptr;
+  cudaStream_t st = nullptr;
+  char err[512] = {0};
+  void* ws = nullptr;
+  size_t ws_bytes = 0, ws_need = 0;
+  bool bound = false;
+  h3d::Shape shape{};
+  double bytes = 0.0;  // algorithmic-bytes counter of the current call
+};
+
+int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...);
+size_t h3d_tsize(const heat3d_ctx* c);
+void h3d_fill_item(heat3d_ctx* c, int lev, int item, double t0);
+int h3d_upload_items(heat3d_ctx* c, int lev, int b0, int B);
+int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* cvals);
+int h3d_set_item_operators(heat3d_ctx* c, int lev, int b0, int B);
+int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
+                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s);
+int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B);
+int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector<double>* per_item);
+int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_stats* s);
+int h3d_fas_restrict(heat3d_ctx* c, int b0, int B);
+int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B);
+int h3d_spread(heat3d_ctx* c, int lev, int b0, int B, const double* u);
+int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s);
+int h3d_load_dense(heat3d_ctx* c, int lev, const double* src, double* dst_pitched);
+int h3d_store_dense(heat3d_ctx* c, int lev, const double* src_pitched, double* dst);
+void h3d_destroy_extras(heat3d_ctx* c);

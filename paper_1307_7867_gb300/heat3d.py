@@ -1,0 +1,262 @@
+"""Thin ctypes binding of libheat3d.so (the C ABI declared in include/heat3d.h).
+
+Functions carry the ABI's names and only marshal arguments: every step of the
+solver runs in the library's CUDA kernels.  PyTorch provides device memory
+(the context workspace, device arrays) and the CUDA stream.  There is no CPU
+fallback: if the library is missing or no GPU is present, loading fails.
+
+Arrays: dense ``[z][y][x]`` float64 of the N^3 interior values, either CUDA
+tensors (device) or numpy arrays / CPU tensors (host); see the header for
+which arguments accept which.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libheat3d.so")
+
+OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+FP64, MIXED = 0, 1
+FORCING_NONE, FORCING_PAPER_LITERAL, FORCING_EXACT = 0, 1, 2
+
+ABI_FUNCTIONS = [
+    "heat3d_config_default", "heat3d_workspace_size", "heat3d_init", "heat3d_bind_workspace",
+    "heat3d_destroy", "heat3d_last_error", "heat3d_set_stream", "heat3d_apply_laplacian",
+    "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
+    "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
+    "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
+    "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
+]
+
+
+class Heat3DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"heat3d error {code}: {msg}")
+        self.code = code
+
+
+class Level(C.Structure):
+    _fields_ = [("N", C.c_int), ("order", C.c_int), ("M", C.c_int)]
+
+
+class MG(C.Structure):
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double)]
+
+
+class Config(C.Structure):
+    _fields_ = [("nu", C.c_double), ("T", C.c_double), ("dt", C.c_double), ("nlevels", C.c_int),
+                ("levels", Level * 2), ("sweeps_fine", C.c_int), ("sweeps_coarse", C.c_int),
+                ("slices", C.c_int), ("iters", C.c_int), ("tol_sdc", C.c_double),
+                ("predictor", C.c_int), ("mg", MG), ("precision", C.c_int), ("forcing", C.c_int),
+                ("batch", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
+                ("use_graphs", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("vcycles", C.c_longlong), ("solves", C.c_longlong), ("sweeps", C.c_longlong),
+                ("iters", C.c_longlong), ("steps", C.c_longlong), ("notconv", C.c_int),
+                ("residual", C.c_double), ("mg_residual", C.c_double), ("seconds", C.c_double),
+                ("bytes", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("device", C.c_int), ("pool", C.c_void_p), ("pool_bytes", C.c_size_t),
+                ("max_active", C.c_int), ("sweeps", C.c_int), ("precision", C.c_int),
+                ("mg", MG)]
+
+
+class Request(C.Structure):
+    _fields_ = [("N", C.c_int), ("nu", C.c_double), ("T", C.c_double), ("dt", C.c_double),
+                ("nmodes", C.c_int), ("k", (C.c_int * 3) * 8), ("amp", C.c_double * 8)]
+
+
+_lib = None
+
+
+def open_library(path: str = LIB_PATH):
+    """dlopens the library at `path`; raises if it is missing (no CPU fallback exists)."""
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run __graft_entry__.build() (no CPU fallback exists)")
+    return C.CDLL(path)
+
+
+def load():
+    """Loads libheat3d.so once and declares the ABI's argument types."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    L = open_library(LIB_PATH)
+    P, I, D, V = C.POINTER, C.c_int, C.c_double, C.c_void_p
+    L.heat3d_config_default.argtypes = [P(Config)]
+    L.heat3d_config_default.restype = None
+    L.heat3d_workspace_size.argtypes = [P(Config), P(C.c_size_t)]
+    L.heat3d_init.argtypes = [P(Config), P(V)]
+    L.heat3d_bind_workspace.argtypes = [V, V, C.c_size_t]
+    L.heat3d_destroy.argtypes = [V]
+    L.heat3d_last_error.argtypes = [V]
+    L.heat3d_last_error.restype = C.c_char_p
+    L.heat3d_set_stream.argtypes = [V, V]
+    L.heat3d_apply_laplacian.argtypes = [V, I, V, V]
+    L.mg_vcycle.argtypes = [V, I, D, V, V, I, D, P(Stats)]
+    L.heat3d_set_state.argtypes = [V, I, I, D, V]
+    L.heat3d_get_node.argtypes = [V, I, I, I, V]
+    L.heat3d_set_node.argtypes = [V, I, I, I, V]
+    L.sdc_sweep.argtypes = [V, I, I, I, P(Stats)]
+    L.heat3d_sdc_residual.argtypes = [V, I, I, P(D)]
+    L.heat3d_fas_restrict.argtypes = [V, I, I]
+    L.heat3d_fas_interpolate.argtypes = [V, I, I]
+    L.pfasst_run.argtypes = [V, V, V, P(Stats)]
+    if hasattr(L, "heat3d_server_create"):
+        L.heat3d_server_create.argtypes = [P(ServerConfig), P(V)]
+        L.heat3d_submit.argtypes = [V, P(Request), P(C.c_uint64)]
+        L.heat3d_poll.argtypes = [V, C.c_uint64, P(I)]
+        L.heat3d_wait.argtypes = [V, C.c_uint64, V, P(Stats)]
+        L.heat3d_server_latency.argtypes = [V, P(D), P(D), P(C.c_longlong)]
+        L.heat3d_server_destroy.argtypes = [V]
+        L.heat3d_server_last_error.argtypes = [V]
+        L.heat3d_server_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _ptr(a):
+    """Device or host address of a float64 array-like (torch tensor or numpy)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        import torch
+        assert a.dtype == torch.float64 and a.is_contiguous(), "need a contiguous float64 tensor"
+        return C.c_void_p(a.data_ptr())
+    assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+    return C.c_void_p(a.ctypes.data)
+
+
+def _check(rc, ctx=None, allow=()):
+    if rc == OK or rc in allow:
+        return rc
+    msg = load().heat3d_last_error(ctx).decode() if ctx else ""
+    raise Heat3DError(rc, msg)
+
+
+def heat3d_config_default() -> Config:
+    cfg = Config()
+    load().heat3d_config_default(C.byref(cfg))
+    return cfg
+
+
+def heat3d_workspace_size(cfg: Config) -> int:
+    n = C.c_size_t(0)
+    _check(load().heat3d_workspace_size(C.byref(cfg), C.byref(n)))
+    return n.value
+
+
+class Context:
+    """A heat3d context with a torch-allocated workspace bound to it."""
+
+    def __init__(self, cfg: Config, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("heat3d needs a CUDA device (no CPU fallback)")
+        L = load()
+        self.cfg = cfg
+        dev = torch.device("cuda", cfg.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        cfg.stream = C.c_void_p(self.stream.cuda_stream)
+        h = C.c_void_p()
+        _check(L.heat3d_init(C.byref(cfg), C.byref(h)))
+        self.h = h
+        nbytes = heat3d_workspace_size(cfg)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=dev)
+        _check(L.heat3d_bind_workspace(h, C.c_void_p(self.workspace.data_ptr()), nbytes), h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().heat3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return load().heat3d_last_error(self.h).decode()
+
+
+def heat3d_apply_laplacian(ctx: Context, level, u, out):
+    return _check(load().heat3d_apply_laplacian(ctx.h, level, _ptr(u), _ptr(out)), ctx.h)
+
+
+def mg_vcycle(ctx: Context, level, c, rhs, u, max_cycles, tol, allow_notconv=False):
+    st = Stats()
+    rc = load().mg_vcycle(ctx.h, level, float(c), _ptr(rhs), _ptr(u), int(max_cycles), float(tol),
+                          C.byref(st))
+    _check(rc, ctx.h, allow=(ENOTCONV,) if allow_notconv else ())
+    return rc, st.as_dict()
+
+
+def heat3d_set_state(ctx: Context, level, item, t0, u0):
+    return _check(load().heat3d_set_state(ctx.h, level, item, float(t0), _ptr(u0)), ctx.h)
+
+
+def heat3d_get_node(ctx: Context, level, item, node, out):
+    return _check(load().heat3d_get_node(ctx.h, level, item, node, _ptr(out)), ctx.h)
+
+
+def heat3d_set_node(ctx: Context, level, item, node, arr):
+    return _check(load().heat3d_set_node(ctx.h, level, item, node, _ptr(arr)), ctx.h)
+
+
+def sdc_sweep(ctx: Context, level, batch_begin, batch_count, allow_notconv=False):
+    st = Stats()
+    rc = load().sdc_sweep(ctx.h, level, batch_begin, batch_count, C.byref(st))
+    _check(rc, ctx.h, allow=(ENOTCONV,) if allow_notconv else ())
+    return rc, st.as_dict()
+
+
+def heat3d_sdc_residual(ctx: Context, level, item) -> float:
+    r = C.c_double(0.0)
+    _check(load().heat3d_sdc_residual(ctx.h, level, item, C.byref(r)), ctx.h)
+    return r.value
+
+
+def heat3d_fas_restrict(ctx: Context, begin, count):
+    return _check(load().heat3d_fas_restrict(ctx.h, begin, count), ctx.h)
+
+
+def heat3d_fas_interpolate(ctx: Context, begin, count):
+    return _check(load().heat3d_fas_interpolate(ctx.h, begin, count), ctx.h)
+
+
+def pfasst_run(ctx: Context, u0, uT, allow_notconv=False):
+    st = Stats()
+    rc = load().pfasst_run(ctx.h, _ptr(u0), _ptr(uT), C.byref(st))
+    _check(rc, ctx.h, allow=(ENOTCONV,) if allow_notconv else ())
+    return rc, st.as_dict()
+
+
+def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2, sweeps_coarse=1,
+                slices=1, iters=20, tol_sdc=1e-10, predictor=1, nu1=2, nu2=1, max_cycles=50,
+                mg_tol=1e-10, precision=FP64, forcing=FORCING_PAPER_LITERAL, batch=1, device=0,
+                use_graphs=0) -> Config:
+    """fine, coarse: (N, order, M) tuples; coarse None gives single-level SDC."""
+    cfg = heat3d_config_default()
+    cfg.nu, cfg.T, cfg.dt = nu, T, dt
+    cfg.nlevels = 1 if coarse is None else 2
+    cfg.levels[0] = Level(*fine)
+    if coarse is not None:
+        cfg.levels[1] = Level(*coarse)
+    cfg.sweeps_fine, cfg.sweeps_coarse = sweeps_fine, sweeps_coarse
+    cfg.slices, cfg.iters, cfg.tol_sdc, cfg.predictor = slices, iters, tol_sdc, predictor
+    cfg.mg = MG(nu1, nu2, max_cycles, mg_tol)
+    cfg.precision, cfg.forcing, cfg.batch, cfg.device = precision, forcing, batch, device
+    cfg.use_graphs = use_graphs
+    return cfg

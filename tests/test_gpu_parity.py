@@ -1,0 +1,229 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances: FP64 path 1e-11 relative max-norm (element by element); mixed
+precision 1e-9 of the FP64 oracle after refinement.  Sizes span several
+32 x 4 thread tiles with ragged tails (N = 63, 127 against tile widths of 32
+and chunks of 16 planes) and include the one-unknown grid (N = 1).
+"""
+import numpy as np
+import pytest
+
+from paper_1307_7867_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def H():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1307_7867_gb300 import build, heat3d
+    build.build()
+    heat3d.load()
+    return heat3d
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("N", [1, 3, 7, 31, 63, 127])
+def test_laplacian(H, oracle, order, N):
+    cfg = H.make_config((N, order, 3), nu=0.1)
+    ctx = H.Context(cfg)
+    u = inputs.random_field(N, seed=100 + N)
+    out = torch.empty(N, N, N, dtype=torch.float64, device="cuda")
+    H.heat3d_apply_laplacian(ctx, 0, dev(u), out)
+    ref = 0.1 * oracle.laplacian(u, order)
+    assert rel(host(out), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("order", [2, 4])
+@pytest.mark.parametrize("N,c,cycles", [(1, 0.3, 1), (3, 0.05, 2), (15, 0.01, 3), (63, 0.002, 2),
+                                        (127, 0.0005, 1)])
+def test_mg_fixed_cycles_fp64(H, oracle, order, N, c, cycles):
+    """V(2,1) cycles in FP64 equal the oracle's cycles (fixed count)."""
+    cfg = H.make_config((N, order, 3))
+    ctx = H.Context(cfg)
+    b = inputs.random_field(N, seed=1)
+    u0 = inputs.random_field(N, seed=2, scale=0.1)
+    u = dev(u0)
+    H.mg_vcycle(ctx, 0, c, dev(b), u, cycles, -1.0)
+    ref, rc, cyc, res = oracle.mg_solve(u0, b, order, c, tol=-1.0, max_cycles=cycles)
+    assert rel(host(u), ref) <= 1e-11
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_mg_tolerance_and_notconv(H, oracle, order):
+    N, c = 31, 0.01
+    cfg = H.make_config((N, order, 3))
+    ctx = H.Context(cfg)
+    b = inputs.random_field(N, seed=3)
+    u = dev(np.zeros_like(b))
+    rc, st = H.mg_vcycle(ctx, 0, c, dev(b), u, 50, 1e-12)
+    ref, orc, ocyc, ores = oracle.mg_solve(np.zeros_like(b), b, order, c, tol=1e-12, max_cycles=50)
+    assert st["vcycles"] == ocyc
+    assert rel(host(u), ref) <= 1e-11
+    assert st["mg_residual"] <= 1e-12
+    u2 = dev(np.zeros_like(b))
+    rc, st = H.mg_vcycle(ctx, 0, c, dev(b), u2, 2, 1e-14, allow_notconv=True)
+    assert rc == H.ENOTCONV and st["notconv"] == 1
+
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_mg_mixed_precision_refinement(H, oracle, order):
+    """FP32 V-cycles inside FP64 residual refinement reach the FP64 solution to 1e-9."""
+    N, c = 63, 0.002
+    cfg = H.make_config((N, order, 3), precision=H.MIXED)
+    ctx = H.Context(cfg)
+    b = inputs.random_field(N, seed=4)
+    u = dev(np.zeros_like(b))
+    rc, st = H.mg_vcycle(ctx, 0, c, dev(b), u, 60, 1e-12)
+    ref, _, ocyc, _ = oracle.mg_solve(np.zeros_like(b), b, order, c, tol=1e-13, max_cycles=80)
+    assert rel(host(u), ref) <= 1e-9
+    assert st["vcycles"] <= ocyc + 3
+
+
+PROB = dict(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-12, mg_max=50)
+
+
+@pytest.mark.parametrize("N,order,M", [(31, 2, 3), (15, 4, 5), (63, 4, 5)])
+def test_sdc_sweep(H, oracle, N, order, M):
+    """One sweep from a spread initial value, then a second one, node by node."""
+    cfg = H.make_config((N, order, M), dt=1.0 / 16, mg_tol=1e-12)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(N, seed=5, kmax=6)
+    t0 = 0.25
+    H.heat3d_set_state(ctx, 0, 0, t0, u0)
+    prob = oracle.Prob(**PROB)
+    U, F = oracle.spread(N, order, M, prob, u0)
+    for sweep in range(2):
+        H.sdc_sweep(ctx, 0, 0, 1)
+        U, F, rc, st = oracle.sdc_sweep(N, order, M, prob, t0, 1.0 / 16, U, F)
+        out = np.empty((N, N, N))
+        for m in range(M):
+            H.heat3d_get_node(ctx, 0, 0, m, out)
+            assert rel(out, U[m]) <= 1e-11, (sweep, m)
+    r = H.heat3d_sdc_residual(ctx, 0, 0)
+    ro = oracle.sdc_residual(N, order, M, prob, t0, 1.0 / 16, U, F)
+    assert abs(r - ro) <= 1e-11 * max(1.0, ro) + 1e-14
+
+
+def test_sdc_batched_items_match_single(H, oracle):
+    """Three items swept in one batch equal each item swept alone (masks are per item)."""
+    N, order, M = 31, 4, 5
+    cfg = H.make_config((N, order, M), dt=1.0 / 32, batch=3, mg_tol=1e-11)
+    ctx = H.Context(cfg)
+    us = [inputs.smooth_random_field(N, seed=s, kmax=5) * (1 + s) for s in range(3)]
+    for i, u in enumerate(us):
+        H.heat3d_set_state(ctx, 0, i, 0.1 * i, u)
+    H.sdc_sweep(ctx, 0, 0, 3)
+    got = []
+    for i in range(3):
+        o = np.empty((N, N, N))
+        H.heat3d_get_node(ctx, 0, i, M - 1, o)
+        got.append(o)
+    for i, u in enumerate(us):
+        H.heat3d_set_state(ctx, 0, 0, 0.1 * i, u)
+        H.sdc_sweep(ctx, 0, 0, 1)
+        o = np.empty((N, N, N))
+        H.heat3d_get_node(ctx, 0, 0, M - 1, o)
+        assert np.array_equal(o, got[i])
+
+
+def test_fas_restrict_coarse_sweep_interpolate(H, oracle):
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    dt, t0 = 1.0 / 16, 0.5
+    cfg = H.make_config(fine, coarse, dt=dt, mg_tol=1e-12)
+    ctx = H.Context(cfg)
+    prob = oracle.Prob(**PROB)
+    u0 = inputs.smooth_random_field(31, seed=7, kmax=6)
+    H.heat3d_set_state(ctx, 0, 0, t0, u0)
+    H.heat3d_set_state(ctx, 1, 0, t0, np.zeros((15, 15, 15)))
+    H.sdc_sweep(ctx, 0, 0, 1)
+    UF, FF = oracle.spread(*fine, prob, u0)
+    UF, FF, _, _ = oracle.sdc_sweep(*fine, prob, t0, dt, UF, FF)
+    H.heat3d_fas_restrict(ctx, 0, 1)
+    UG, FG, UGr, tQ = oracle.fas_restrict(fine, coarse, prob, t0, dt, UF, FF)
+    og = np.empty((15, 15, 15))
+    for m in range(3):
+        H.heat3d_get_node(ctx, 1, 0, m, og)
+        assert rel(og, UG[m]) <= 1e-14
+    rg = H.heat3d_sdc_residual(ctx, 1, 0)
+    assert abs(rg - oracle.sdc_residual(*coarse, prob, t0, dt, UG, FG, tQ)) <= 1e-12
+    H.sdc_sweep(ctx, 1, 0, 1)
+    UG2, FG2, _, _ = oracle.sdc_sweep(*coarse, prob, t0, dt, UG, FG, tQ)
+    for m in range(3):
+        H.heat3d_get_node(ctx, 1, 0, m, og)
+        assert rel(og, UG2[m]) <= 1e-11
+    H.heat3d_fas_interpolate(ctx, 0, 1)
+    UF2, FF2 = oracle.fas_interpolate(fine, coarse, prob, UG2, UGr, UF)
+    of = np.empty((31, 31, 31))
+    for j in range(5):
+        H.heat3d_get_node(ctx, 0, 0, j, of)
+        assert rel(of, UF2[j]) <= 1e-11
+
+
+def test_run_config1_sdc(H, oracle):
+    """Plain serial SDC at the 31^3 / 7-point / 3-node / dt = 1/8 / 4-sweep setup, T = 1."""
+    N = 31
+    cfg = H.make_config((N, 2, 3), dt=0.125, T=1.0, sweeps_fine=4, tol_sdc=-1.0, mg_tol=1e-10)
+    ctx = H.Context(cfg)
+    u0 = inputs.sine_mode(N)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, orc, ost = oracle.sdc_run(N, 2, 3, oracle.Prob(mg_tol=1e-10), 0.125, 8, 4, u0)
+    assert rel(uT, ref) <= 1e-11
+    assert st["sweeps"] == ost["sweeps"] and st["vcycles"] == ost["vcycles"]
+
+
+def test_run_mlsdc_small(H, oracle):
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
+                        mg_tol=1e-11)
+    ctx = H.Context(cfg)
+    u0 = inputs.sine_mode(31)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, orc, ost = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11), 1 / 64, 2, u0,
+                                     nsweeps_fine=2, max_iters=20, tol=1e-10)
+    assert st["iters"] == ost["iters"]
+    assert rel(uT, ref) <= 1e-11
+
+
+@pytest.mark.parametrize("P,K", [(4, 3), (8, 2)])
+def test_run_pfasst_small(H, oracle, P, K):
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 16, T=P / 16, sweeps_fine=1, slices=P, iters=K,
+                        tol_sdc=-1.0, mg_tol=1e-12)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(15, seed=9, kmax=4)
+    uT = np.empty_like(u0)
+    H.pfasst_run(ctx, u0, uT)
+    ref, _, _ = oracle.pfasst_run(fine, coarse, oracle.Prob(mg_tol=1e-12), 1 / 16, P, P, u0,
+                                  nsweeps_fine=1, max_iters=K)
+    assert rel(uT, ref) <= 1e-11
+
+
+def test_run_mixed_precision_matches_fp64_oracle(H, oracle):
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, precision=H.MIXED, mg_tol=1e-11)
+    ctx = H.Context(cfg)
+    u0 = inputs.sine_mode(31)
+    uT = np.empty_like(u0)
+    H.pfasst_run(ctx, u0, uT)
+    ref, _, _ = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11), 1 / 32, 2, u0,
+                                 nsweeps_fine=2, max_iters=20, tol=1e-10)
+    assert rel(uT, ref) <= 1e-9
