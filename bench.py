@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput of the SDC / MLSDC / PFASST hot path on one GB300, in grid-point
+time steps per second (N_fine^3 x time steps / second).
+
+Default workload (one "step" = one time step of two-level MLSDC):
+  fine 255^3, 4th-order wide Laplacian, 5 Gauss-Lobatto nodes; coarse 127^3,
+  7-point Laplacian, 3 nodes; nu = 0.1, dt = 1/64, forcing of Eq. 3 as printed,
+  initial value sin(pi x) sin(pi y) sin(pi z); each step iterates [2 fine
+  sweeps, FAS restriction, 1 coarse sweep, interpolation] until the fine
+  collocation residual is <= 1e-10 (at most 20 iterations); every implicit
+  substep is solved by V(2,1) multigrid to max|b - A u| <= 1e-11.  FP64.
+
+Other workloads: --workload c1 | c3 | c4 (see WORKLOADS).
+
+Timed region: K steps in one pfasst_run call on device-resident buffers,
+bracketed by barrier + synchronize, CUDA events on the context's stream.  The
+working set (dozens of 133 MB fields) is far larger than L2, so no flush is
+needed between steps.  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Fine-level V-cycles per MLSDC step of the default workload, counted on a
+# full GB300 run (the oracle performs the same cycles: the parity tests check
+# equal counts).  Used only by --impl reference to scale its timed sample.
+REF_FINE_VCYCLES_PER_STEP = 240.0
+REF_COARSE_VCYCLES_PER_STEP = 40.0
+
+WORKLOADS = {
+    "c2": dict(
+        desc="two-level MLSDC, fine 255^3 wide M=5 / coarse 127^3 7-point M=3, dt=1/64, "
+             "2 fine sweeps per iteration, residual 1e-10 (<= 20 iterations), V(2,1) to 1e-11",
+        fine=(255, 4, 5), coarse=(127, 2, 3), dt=1 / 64, sweeps_fine=2, sweeps_coarse=1,
+        slices=1, iters=20, tol_sdc=1e-10, mg_tol=1e-11, precision="fp64", steps=6, warmup=3),
+    "c1": dict(
+        desc="serial SDC, 31^3 7-point M=3, dt=1/8, 4 sweeps per step, V(2,1) to 1e-10",
+        fine=(31, 2, 3), coarse=None, dt=1 / 8, sweeps_fine=4, sweeps_coarse=0, slices=1,
+        iters=0, tol_sdc=-1.0, mg_tol=1e-10, precision="fp64", steps=8, warmup=3),
+    "c3": dict(
+        desc="PFASST, 16 slices batched, fine 127^3 wide M=5 / coarse 63^3 7-point M=3, "
+             "dt=1/16, 5 iterations, 1 fine sweep per iteration",
+        fine=(127, 4, 5), coarse=(63, 2, 3), dt=1 / 16, sweeps_fine=1, sweeps_coarse=1,
+        slices=16, iters=5, tol_sdc=-1.0, mg_tol=1e-11, precision="fp64", steps=16, warmup=16),
+    "c4": dict(
+        desc="mixed precision, fine 511^3 wide M=5 / coarse 255^3 7-point M=3, dt=1/32, "
+             "MLSDC to residual 1e-10, FP32 V-cycles in FP64 refinement to 1e-11",
+        fine=(511, 4, 5), coarse=(255, 2, 3), dt=1 / 32, sweeps_fine=2, sweeps_coarse=1,
+        slices=1, iters=20, tol_sdc=1e-10, mg_tol=1e-11, precision="mixed", steps=2, warmup=1),
+}
+
+
+def analytic_amplitude(t, nu=0.1, kappa=1.0, lam=None):
+    """Mode amplitude of u = a(t) Phi for a' = lam a - (sin t - kappa nu pi^2 cos t), a(0)=1;
+    lam = -3 nu pi^2 gives the PDE's exact solution (Eqs. 3-4)."""
+    c = 3 * nu * math.pi ** 2 if lam is None else -lam
+    d = kappa * nu * math.pi ** 2
+    A = (1 + c * d) / (1 + c * c)
+    B = (d - c) / (1 + c * c)
+    return A * math.cos(t) + B * math.sin(t) + (1 - A) * math.exp(-c * t)
+
+
+def wide_lambda(N, nu=0.1):
+    h = 1.0 / (N + 1)
+    th = math.pi * h
+    return nu * 3 * (-2 * math.cos(2 * th) + 32 * math.cos(th) - 30) / (12 * h * h)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.p:
+            return None
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, r in rows for k in range(4) if r[k].lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+def make_cfg(H, w, precision=None, slices=None):
+    prec = H.MIXED if (precision or w["precision"]) == "mixed" else H.FP64
+    return H.make_config(w["fine"], w["coarse"], dt=w["dt"], T=w["dt"],
+                         sweeps_fine=w["sweeps_fine"], sweeps_coarse=w["sweeps_coarse"],
+                         slices=slices or w["slices"], iters=w["iters"], tol_sdc=w["tol_sdc"],
+                         mg_tol=w["mg_tol"], max_cycles=50, precision=prec,
+                         forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"])
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args, w, rank, world):
+    import torch
+    import torch.distributed as dist
+    from paper_1307_7867_gb300 import build, heat3d as H, inputs
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    Nf = w["fine"][0]
+    u0 = inputs.sine_mode(Nf)
+    u0_d = torch.from_numpy(u0).to(dev)
+    uT_d = torch.empty_like(u0_d)
+    P = w["slices"]
+    K, W = args.steps, args.warmup
+    if K % P or W % P:
+        raise SystemExit(f"--steps and --warmup must be multiples of the {P} slices")
+    dt = w["dt"]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx = H.Context(make_cfg(H, w))
+    # warm-up steps (untimed)
+    H.heat3d_set_interval(ctx, 0.0, W * dt)
+    H.pfasst_run(ctx, u0_d, uT_d, allow_notconv=True)
+    # timed steps: K steps from t = 0 on device-resident buffers
+    prof_class = H.PROF_JACOBI_FINE if w["precision"] == "fp64" else H.PROF_RESID64_FINE
+    H.heat3d_profile(ctx, prof_class)
+    H.heat3d_set_interval(ctx, 0.0, K * dt)
+    launches0 = H.heat3d_kernel_launches()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(dev.index) as clk:
+        ev0.record(ctx.stream)
+        rc, st = H.pfasst_run(ctx, u0_d, uT_d, allow_notconv=True)
+        ev1.record(ctx.stream)
+        barrier()
+    launches = H.heat3d_kernel_launches() - launches0
+    ms = ev0.elapsed_time(ev1)
+    prof = H.heat3d_profile_read(ctx)
+    H.heat3d_profile(ctx, H.PROF_OFF)
+    secs = ms / 1e3
+    if world > 1:
+        t = torch.tensor([secs], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        secs = float(t.item())
+    pts = float(Nf) ** 3
+    value = world * pts * K / secs
+    uT = uT_d.cpu().numpy()
+
+    # accuracy against the exact PDE solution and the semi-discrete solution
+    phi = inputs.sine_mode(Nf)
+    tK = K * dt
+    a_pde = analytic_amplitude(tK)
+    err_pde = float(np.abs(uT - a_pde * phi).max() / abs(a_pde))
+    lam = wide_lambda(Nf) if w["fine"][1] == 4 else 0.1 * 3 * (2 * math.cos(math.pi / (Nf + 1)) - 2) * (Nf + 1) ** 2
+    a_sd = analytic_amplitude(tK, lam=lam)
+    err_sd = float(np.abs(uT - a_sd * phi).max() / abs(a_sd))
+
+    # end to end through the C ABI with pinned host buffers: per step, H2D of
+    # the step's initial value, the step, D2H of its result
+    uh = torch.from_numpy(u0.copy()).pin_memory()
+    uo = torch.empty_like(uh).pin_memory()
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(0, K, P):
+        H.heat3d_set_interval(ctx, s * dt, P * dt)
+        H.pfasst_run(ctx, uh, uo, allow_notconv=True)
+        uh, uo = uo, uh
+    barrier()
+    e2e_secs = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_secs], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_secs = float(t.item())
+    e2e_diff = float(np.abs(uh.numpy() - uT).max())
+    nbytes = Nf ** 3 * 8
+
+    pk, pk_src = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    if prof["launches"] > 0 and prof["ms"] > 0:
+        per_launch_s = prof["ms"] / 1e3 / prof["launches"]
+        dp_per_launch = prof["dp_ops"] / prof["launches"]
+        fp64_peak = 152 * 2 * sm_max * 1e6 / 1e9  # Gop/s: 2 FP64 pipe ops / clk / SM
+        if w["precision"] == "fp64" or prof_class == H.PROF_RESID64_FINE:
+            achieved = dp_per_launch / per_launch_s / 1e9
+            roof = {"bound": "alu", "kernel": "jacobi_fine_fp64" if prof_class == 1 else "resid64_fine",
+                    "achieved": round(achieved, 2), "peak": round(fp64_peak, 1),
+                    "unit": "Gop/s (FP64 pipe)", "frac": round(achieved / fp64_peak, 4),
+                    "peak_source": f"152 SMs x 2 FP64 ops/clk x {sm_max:.0f} MHz",
+                    "hbm_achieved_gbs": round(prof["bytes"] / prof["launches"] / per_launch_s / 1e9, 1),
+                    "hbm_frac_of_measured": round(prof["bytes"] / prof["launches"] / per_launch_s / 1e9
+                                                  / pk["hbm_gbs"], 4),
+                    "launches": prof["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
+                    "traffic": None}
+        else:
+            gbs = prof["bytes"] / prof["launches"] / per_launch_s / 1e9
+            roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": round(gbs / pk["hbm_gbs"], 4), "traffic": None}
+        roof["peak_file"] = pk_src
+    else:
+        roof = None
+
+    out = {
+        "metric": "grid-pt-steps/s at fixed error",
+        "value": value, "unit": "grid-pt-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "f64+f32",
+        "data": "synthetic (analytic initial value and forcing, Eqs. 3-4)",
+        "config": {"workload": w["desc"], "N_fine": Nf, "dt": dt,
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "working set >> L2 (fields of 133 MB+), no flush needed"},
+        "stats": {k: st[k] for k in ("vcycles", "vcycles_level", "solves", "sweeps", "iters",
+                                     "notconv", "residual")},
+        "accuracy": {"rel_err_vs_pde_solution": err_pde, "rel_err_vs_semidiscrete": err_sd,
+                     "t_end": tK},
+        "roofline": roof,
+        "e2e": {"value": world * pts * K / e2e_secs, "unit": "grid-pt-steps/s",
+                "h2d_bytes_per_step": nbytes * 1.0 / P, "d2h_bytes_per_step": nbytes * 1.0 / P,
+                "max_abs_diff_vs_device_run": e2e_diff},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    return out, ctx, st, u0, uT
+
+
+def oracle_sample_fine_vcycle(w):
+    """Seconds per fine V-cycle (with its residual check) of the oracle at full size."""
+    from oracle import oracle as O
+    from paper_1307_7867_gb300 import inputs
+    Nf, order, M = w["fine"]
+    tau1 = O.gl_nodes(M)[1]
+    c = w["dt"] * tau1 * 0.1
+    b = inputs.sine_mode(Nf)
+    u = np.zeros_like(b)
+    t0 = time.perf_counter()
+    O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=1)
+    t1 = time.perf_counter()
+    O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=2)
+    t2 = time.perf_counter()
+    return (t2 - t1) - (t1 - t0), (t2 - t0)
+
+
+def cpu_baseline(w, fine_v, coarse_v, sample_desc_extra=""):
+    per_v, spent = oracle_sample_fine_vcycle(w)
+    t_step = per_v * (fine_v + coarse_v / 8.0)
+    Nf = w["fine"][0]
+    return {"value": Nf ** 3 / t_step, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle (single-thread C, FP64) timed for 1 and 2 V(2,1) cycles of a fine "
+                       f"{Nf}^3 solve ({spent:.1f} s); per step = seconds per fine V-cycle x "
+                       f"({fine_v:.0f} fine + {coarse_v:.0f}/8 coarse V-cycles per step)"
+                       f"{sample_desc_extra}; quadrature, FAS and transfer work excluded, "
+                       f"so the CPU figure is optimistic")}
+
+
+def run_reference(args, w):
+    """The oracle on the machine's host cores: each step is one fine V-cycle at full size,
+    scaled to grid-pt-steps/s by the V-cycles one step of this workload performs."""
+    from oracle import oracle as O
+    O.build()
+    times = []
+    for s in range(args.warmup + args.steps):
+        per_v, _ = oracle_sample_fine_vcycle(w)
+        if s >= args.warmup:
+            times.append(per_v)
+    per_v = sum(times) / len(times)
+    t_step = per_v * (REF_FINE_VCYCLES_PER_STEP + REF_COARSE_VCYCLES_PER_STEP / 8.0)
+    Nf = w["fine"][0]
+    v = Nf ** 3 / t_step
+    return {"impl": "reference", "metric": "grid-pt-steps/s at fixed error", "value": v,
+            "unit": "grid-pt-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["desc"]},
+            "cpu_baseline": {"value": v, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle",
+                             "sample": "per step: one fine V(2,1) cycle of the oracle at full size, "
+                                       f"scaled by {REF_FINE_VCYCLES_PER_STEP:.0f} fine + "
+                                       f"{REF_COARSE_VCYCLES_PER_STEP:.0f}/8 coarse V-cycles per step"},
+            "e2e": {"value": v, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=None)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    args.steps = args.steps or w["steps"]
+    args.warmup = w["warmup"] if args.warmup is None else args.warmup
+    if args.warmup < 3 and w["slices"] == 1:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, w)), flush=True)
+        return
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out, ctx, st, u0, uT = run_ours(args, w, rank, world)
+
+    if rank == 0 and world == 1 and not args.no_mixed and w["precision"] == "fp64" and w["coarse"]:
+        # the same workload with FP32 V-cycles inside FP64 refinement
+        import torch
+        from paper_1307_7867_gb300 import heat3d as H
+        cm = H.Context(make_cfg(H, w, precision="mixed"))
+        u0_d = torch.from_numpy(u0).cuda()
+        o = torch.empty_like(u0_d)
+        H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
+        H.pfasst_run(cm, u0_d, o, allow_notconv=True)
+        H.heat3d_set_interval(cm, 0.0, args.steps * w["dt"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cm.stream)
+        rc, sm = H.pfasst_run(cm, u0_d, o, allow_notconv=True)
+        e1.record(cm.stream)
+        torch.cuda.synchronize()
+        s_m = e0.elapsed_time(e1) / 1e3
+        um = o.cpu().numpy()
+        Nf = w["fine"][0]
+        a_pde = analytic_amplitude(args.steps * w["dt"])
+        from paper_1307_7867_gb300 import inputs
+        err_m = float(np.abs(um - a_pde * inputs.sine_mode(Nf)).max() / abs(a_pde))
+        out["mixed"] = {"value": Nf ** 3 * args.steps / s_m, "ms_per_step": s_m * 1e3 / args.steps,
+                        "rel_err_vs_pde_solution": err_m,
+                        "max_rel_diff_vs_fp64": float(np.abs(um - uT).max() / np.abs(uT).max()),
+                        "vcycles": sm["vcycles"], "iters": sm["iters"],
+                        "equal_error": err_m <= 1.01 * out["accuracy"]["rel_err_vs_pde_solution"]}
+        cm.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        fv = st["vcycles_level"][0] / max(args.steps, 1)
+        cv = st["vcycles_level"][1] / max(args.steps, 1)
+        out["cpu_baseline"] = cpu_baseline(w, fv, cv)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -98,6 +98,7 @@ typedef struct {
   double mg_residual;  /* last multigrid residual max|b - A u| */
   double seconds;      /* device time of the call, from CUDA events on the stream */
   double bytes;        /* algorithmic HBM bytes of the call's kernels (a counter) */
+  long long vcycles_level[2]; /* V-cycles of solves on SDC level 0 (fine) and 1 (coarse) */
 } heat3d_stats;
 
 typedef struct heat3d_ctx heat3d_ctx;
@@ -164,10 +165,33 @@ int heat3d_sdc_residual(heat3d_ctx* ctx, int level, int item, double* residual);
 int heat3d_fas_restrict(heat3d_ctx* ctx, int begin, int count);
 int heat3d_fas_interpolate(heat3d_ctx* ctx, int begin, int count);
 
-/* Integrates from t = 0 to cfg.T: single-level SDC (nlevels = 1), MLSDC
+/* Sets the interval pfasst_run integrates: [t0, t0 + T] (T a multiple of
+ * cfg.dt and of slices * dt).  The default is [0, cfg.T]. */
+int heat3d_set_interval(heat3d_ctx* ctx, double t0, double T);
+
+/* Integrates over [t0, t0 + T] (heat3d_set_interval; default [0, cfg.T]): single-level SDC (nlevels = 1), MLSDC
  * (slices = 1) or PFASST on blocks of `slices` time slices (Sec. 1.1).
  * u0 in, uT out: host or device, dense N_fine^3 FP64. */
 int pfasst_run(heat3d_ctx* ctx, const double* u0, double* uT, heat3d_stats* stats);
+
+/* ---------------------------------------------------------------------- */
+/* Diagnostics (no counterpart in the paper).                               */
+/* ---------------------------------------------------------------------- */
+
+/* Kernels this library has launched in the process so far (all contexts). */
+long long heat3d_kernel_launches(void);
+
+#define HEAT3D_PROF_OFF 0
+#define HEAT3D_PROF_JACOBI_FINE 1 /* damped-Jacobi sweeps on the finest multigrid level of SDC level 0 */
+#define HEAT3D_PROF_RESID64_FINE 2 /* FP64 refinement residual on SDC level 0 */
+/* Brackets every launch of one kernel class with CUDA events on the context's
+ * stream from now on (HEAT3D_PROF_OFF stops and clears). */
+int heat3d_profile(heat3d_ctx* ctx, int kernel_class);
+/* Totals since heat3d_profile: summed device milliseconds, launches, and the
+ * algorithmic bytes, FP64 pipe operations and flops of those launches.
+ * Synchronises the stream. */
+int heat3d_profile_read(heat3d_ctx* ctx, double* ms, long long* launches, double* bytes,
+                        double* dp_ops, double* flops);
 
 /* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of independent heat-equation solves.        */

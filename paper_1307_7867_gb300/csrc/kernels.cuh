@@ -14,6 +14,9 @@ struct Shape {
   int bx = 32, by = 4, zc = 16;
 };
 
+// Process-wide count of kernel launches (every launcher calls it once per launch).
+void count_launch();
+
 // ---- spatial operator (Sec. 1, method of lines) ----
 // out = alpha_b * L u with L = (S1 - 6u) (order 2) or (16 S1 - S2 - 90u)
 // (order 4); alpha_b = nu_b / h^2 or nu_b / (12 h^2).  When add_src != nullptr

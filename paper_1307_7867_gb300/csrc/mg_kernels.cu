@@ -201,6 +201,7 @@ cudaError_t run_zmarch(const Grid& g, int B, const int* active, unsigned long lo
   dim3 blk(sh.bx, sh.by, 1);
   dim3 grd((g.N + sh.bx - 1) / sh.bx, (g.N + sh.by - 1) / sh.by, nzc * B);
   k_zmarch<T, ORDER, Op><<<grd, blk, 0, st>>>(g, nzc, zc, active, norm_bits, op);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -406,6 +407,7 @@ cudaError_t launch_jacobi_zero(const Grid& g, int B, const T* r, T* e, const Coe
   if (B <= 0) return cudaSuccess;
   k_jacobi_zero<T><<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, r, e, coef, exact ? 1 : 0,
                                                               active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -414,6 +416,7 @@ cudaError_t launch_restrict(const Grid& gf, const Grid& gc, int B, const T* rr, 
                             const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_restrict<T><<<point_grid(gc, B), dim3(32, 8), 0, st>>>(gf, gc, rr, bc, active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -424,6 +427,7 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
   if (B <= 0) return cudaSuccess;
   k_prolong_add<T><<<point_grid(gf, B), dim3(32, 8), 0, st>>>(gc, gf, ec, ec_stride, uf,
                                                               uf_stride, active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -432,6 +436,7 @@ cudaError_t launch_update(const Grid& g, int B, const T* e, double* u64, long lo
                           const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_update<T><<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, e, u64, u64_stride, active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -439,6 +444,7 @@ cudaError_t launch_maxabs(const Grid& g, int B, const double* u, long long u_str
                           unsigned long long* norm_bits, const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_maxabs<<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, u, u_stride, norm_bits, active);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -446,6 +452,7 @@ cudaError_t launch_dense_to_pitched(const Grid& g, int B, const double* dense, d
                                     long long f_stride, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_dense_to_pitched<<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, dense, f, f_stride);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -453,6 +460,7 @@ cudaError_t launch_pitched_to_dense(const Grid& g, int B, const double* f, long 
                                     double* dense, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_pitched_to_dense<<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, f, f_stride, dense);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -460,6 +468,7 @@ cudaError_t launch_copy(const Grid& g, int B, const double* src, long long src_s
                         double* dst, long long dst_stride, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   k_copy<<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, src, src_stride, dst, dst_stride);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "../../include/heat3d.h"
@@ -49,6 +50,43 @@ int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...) {
     int r_ = (call);                       \
     if (r_ < 0) return r_;                 \
   } while (0)
+
+namespace h3d {
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace h3d
+
+int h3d_prof_begin(heat3d_ctx* c, int cls) {
+  if (c->prof_class == 0 || c->prof_class != cls) return -1;
+  if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
+    for (int k = 0; k < 2; ++k) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      c->prof_ev.push_back(e);
+    }
+  }
+  int pair = (int)c->prof_used++;
+  cudaEventRecord(c->prof_ev[2 * pair], c->st);
+  return pair;
+}
+
+void h3d_prof_end(heat3d_ctx* c, int pair, double bytes, double dpops, double flops) {
+  if (pair < 0) return;
+  cudaEventRecord(c->prof_ev[2 * pair + 1], c->st);
+  c->prof_bytes += bytes;
+  c->prof_dpops += dpops;
+  c->prof_flops += flops;
+  c->prof_launches += 1;
+}
+
+static void prof_harvest(heat3d_ctx* c) {
+  cudaStreamSynchronize(c->st);
+  for (size_t p = 0; p < c->prof_used; ++p) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->prof_ev[2 * p], c->prof_ev[2 * p + 1]) == cudaSuccess) c->prof_ms += ms;
+  }
+  c->prof_used = 0;
+}
 
 static bool is_pow2m1(int N) { return N >= 1 && ((N + 1) & N) == 0; }
 
@@ -363,9 +401,22 @@ static const Coef<T>* coefT(SdcLevel& L, int slot, int k, int b0) {
 // finest level the first smoothing result e_0 = wd * r was written by the
 // residual kernel and the last post-smoothing sweep adds its result to u64.
 // Returns the buffer holding the level's correction (nullptr on level 0).
+// Algorithmic cost per point of one damped-Jacobi sweep (bytes, FP64 pipe
+// operations, flops); `upd` adds the result to the FP64 solution.
+template <typename T>
+static void jacobi_cost(int order, bool upd, double* bytes, double* dp, double* fl) {
+  const double ts = sizeof(T);
+  const double ops = order == 2 ? 8.0 : 14.0;     // neighbour sums + 3 fused multiply-adds
+  const double flops = order == 2 ? 11.0 : 18.0;  // an FMA counts 2
+  *bytes = upd ? 2.0 * ts + 16.0 : 3.0 * ts;
+  *dp = (sizeof(T) == 8 ? ops : 0.0) + (upd ? 1.0 : 0.0);
+  *fl = flops + (upd ? 1.0 : 0.0);
+}
+
 template <typename T>
 static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int B,
                         const int* act, double* u64, long long us, T** result) {
+  const bool prof_here = k == 0 && &L == &c->lv[0];
   const Grid& g = L.mg[k];
   const int order = L.L.order;
   const int nu1 = c->cfg.mg.nu1, nu2 = c->cfg.mg.nu2;
@@ -392,7 +443,13 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   T* cur = e;
   T* oth = t;
   for (int s = 1; s < nu1; ++s) {
+    int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
     CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    if (pr >= 0) {
+      double cb, cd, cfl;
+      jacobi_cost<T>(order, false, &cb, &cd, &cfl);
+      h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
+    }
     c->bytes += 3.0 * ts * pts;
     std::swap(cur, oth);
   }
@@ -404,13 +461,20 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   CK(launch_prolong_add<T>(L.mg[k + 1], g, B, ce, L.mg[k + 1].fs, cur, g.fs, act, st));
   c->bytes += ts * pts * (2.0 + 1.0 / 8.0);
   for (int s = 0; s < nu2; ++s) {
-    if (k == 0 && s == nu2 - 1) {
-      CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, c->shape, st));
+    const bool upd = k == 0 && s == nu2 - 1;
+    int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
+    if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, c->shape, st));
+    else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    if (pr >= 0) {
+      double cb, cd, cfl;
+      jacobi_cost<T>(order, upd, &cb, &cd, &cfl);
+      h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
+    }
+    if (upd) {
       c->bytes += (2.0 * ts + 16.0) * pts;
       *result = nullptr;
       return HEAT3D_OK;
     }
-    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
     c->bytes += 3.0 * ts * pts;
     std::swap(cur, oth);
   }
@@ -462,7 +526,14 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
   std::vector<double> nrm;
   auto residual = [&]() -> int {
     CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
+    int pr = lev == 0 ? h3d_prof_begin(c, HEAT3D_PROF_RESID64_FINE) : -1;
     CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, c->shape, st));
+    if (pr >= 0) {
+      // neighbour sums + 2 FMAs (+ the FP64 e0 multiply when T is double)
+      double dp = (order == 2 ? 7.0 : 13.0) + (sizeof(T) == 8 ? 1.0 : 0.0);
+      double fl = (order == 2 ? 9.0 : 16.0) + 1.0;
+      h3d_prof_end(c, pr, (16.0 + 2.0 * sizeof(T)) * pts, dp * pts, fl * pts);
+    }
     c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
     return HEAT3D_OK;
   };
@@ -480,7 +551,10 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     T* dummy = nullptr;
     RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &dummy));
     ++cycles;
-    if (s) s->vcycles += live;
+    if (s) {
+      s->vcycles += live;
+      s->vcycles_level[lev] += live;
+    }
     RET(residual());
     if (!fixed) {
       RET(read_norms(c, L, b0, B, nrm));
@@ -699,8 +773,8 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
   const heat3d_config& cfg = c->cfg;
   SdcLevel& F = c->lv[0];
   const int P = cfg.nlevels == 2 ? cfg.slices : 1;
-  const int nsteps = (int)llround(cfg.T / cfg.dt);
-  if (fabs(nsteps * cfg.dt - cfg.T) > 1e-9 * std::max(1.0, cfg.T))
+  const int nsteps = (int)llround(c->T_run / cfg.dt);
+  if (nsteps < 1 || fabs(nsteps * cfg.dt - c->T_run) > 1e-9 * std::max(1.0, c->T_run))
     return h3d_fail(c, HEAT3D_EINVAL, "T must be a multiple of dt");
   if (nsteps % P != 0) return h3d_fail(c, HEAT3D_EINVAL, "number of steps must be a multiple of slices");
   if (P > F.B) return h3d_fail(c, HEAT3D_EINVAL, "slices exceed the batch capacity");
@@ -715,7 +789,7 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
     RET(h3d_set_item_operators(c, l, 0, P));
   }
   for (int blk = 0; blk < nsteps / P; ++blk) {
-    const double tb = (double)blk * P * cfg.dt;
+    const double tb = c->t_start + (double)blk * P * cfg.dt;
     for (int l = 0; l < cfg.nlevels; ++l) {
       for (int p = 0; p < P; ++p) h3d_fill_item(c, l, p, tb + p * cfg.dt);
       RET(h3d_upload_items(c, l, 0, P));
@@ -862,6 +936,8 @@ int heat3d_init(const heat3d_config* cfg, heat3d_ctx** out) {
   rc = setup_levels(c);
   if (rc < 0) { delete c; return rc; }
   c->ws_need = plan(c, nullptr);
+  c->t_start = 0.0;
+  c->T_run = cfg->T;
   *out = c;
   return HEAT3D_OK;
 }
@@ -890,8 +966,40 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   return HEAT3D_OK;
 }
 
+int heat3d_set_interval(heat3d_ctx* c, double t0, double T) {
+  if (!c || !(T > 0)) return HEAT3D_EINVAL;
+  c->t_start = t0;
+  c->T_run = T;
+  return HEAT3D_OK;
+}
+
+long long heat3d_kernel_launches(void) { return h3d::g_launches.load(); }
+
+int heat3d_profile(heat3d_ctx* c, int kernel_class) {
+  if (!c || kernel_class < 0 || kernel_class > HEAT3D_PROF_RESID64_FINE) return HEAT3D_EINVAL;
+  cudaStreamSynchronize(c->st);
+  c->prof_used = 0;
+  c->prof_ms = c->prof_bytes = c->prof_dpops = c->prof_flops = 0.0;
+  c->prof_launches = 0;
+  c->prof_class = kernel_class;
+  return HEAT3D_OK;
+}
+
+int heat3d_profile_read(heat3d_ctx* c, double* ms, long long* launches, double* bytes,
+                        double* dp_ops, double* flops) {
+  if (!c) return HEAT3D_EINVAL;
+  prof_harvest(c);
+  if (ms) *ms = c->prof_ms;
+  if (launches) *launches = c->prof_launches;
+  if (bytes) *bytes = c->prof_bytes;
+  if (dp_ops) *dp_ops = c->prof_dpops;
+  if (flops) *flops = c->prof_flops;
+  return HEAT3D_OK;
+}
+
 int heat3d_destroy(heat3d_ctx* c) {
   if (!c) return HEAT3D_EINVAL;
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   h3d_destroy_extras(c);
   delete c;
   return HEAT3D_OK;

@@ -61,7 +61,18 @@ struct heat3d_ctx {
   bool bound = false;
   h3d::Shape shape{};
   double bytes = 0.0;  // algorithmic-bytes counter of the current call
+  double t_start = 0.0, T_run = 0.0;  // interval of pfasst_run
+  // per-launch CUDA-event timing of one kernel class (heat3d_profile)
+  int prof_class = 0;
+  std::vector<cudaEvent_t> prof_ev;  // pairs
+  size_t prof_used = 0;              // pairs recorded and not yet harvested
+  double prof_ms = 0.0, prof_bytes = 0.0, prof_dpops = 0.0, prof_flops = 0.0;
+  long long prof_launches = 0;
 };
+
+// Event bracketing for the profiled kernel class: returns a pair index or -1.
+int h3d_prof_begin(heat3d_ctx* c, int cls);
+void h3d_prof_end(heat3d_ctx* c, int pair, double bytes, double dpops, double flops);
 
 int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...);
 size_t h3d_tsize(const heat3d_ctx* c);

@@ -172,6 +172,7 @@ cudaError_t launch_integrals(int M, const Grid& g, int B, const double* U, const
     case 5: k_integrals<5><<<grd, blk, 0, st>>>(g, U, F, tauS, I, items, phi1d, res_bits, active); break;
     default: return cudaErrorInvalidValue;
   }
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -189,6 +190,7 @@ cudaError_t launch_fas_inject(int MF, int MG, const Grid& gf, const Grid& gg, in
   if (MF == a && MG == b) {                                                             \
     k_fas_inject<a, b><<<grd, blk, 0, st>>>(gf, gg, same, UF, FF, UG, UGr, qF, itF, map, \
                                             phif1d);                                    \
+    count_launch();                                                                     \
     return cudaGetLastError();                                                          \
   }
   H3D_FAS_CASES(X)
@@ -208,6 +210,7 @@ cudaError_t launch_fas_tau(int MG, const Grid& gg, int B, const double* qF, cons
     case 5: k_fas_tau<5><<<grd, blk, 0, st>>>(gg, qF, FG, tauS, itG, phig1d); break;
     default: return cudaErrorInvalidValue;
   }
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -218,6 +221,7 @@ cudaError_t launch_fas_delta(int MF, int MG, const Grid& gg, int B, const double
 #define X(a, b)                                                      \
   if (MF == a && MG == b) {                                          \
     k_fas_delta<a, b><<<grd, blk, 0, st>>>(gg, UG, UGr, D, map);     \
+    count_launch();                                                  \
     return cudaGetLastError();                                       \
   }
   H3D_FAS_CASES(X)

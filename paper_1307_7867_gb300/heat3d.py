@@ -20,6 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libheat3d.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PROF_OFF, PROF_JACOBI_FINE, PROF_RESID64_FINE = 0, 1, 2
 FP64, MIXED = 0, 1
 FORCING_NONE, FORCING_PAPER_LITERAL, FORCING_EXACT = 0, 1, 2
 
@@ -28,6 +29,7 @@ ABI_FUNCTIONS = [
     "heat3d_destroy", "heat3d_last_error", "heat3d_set_stream", "heat3d_apply_laplacian",
     "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
     "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
+    "heat3d_set_interval", "heat3d_kernel_launches", "heat3d_profile", "heat3d_profile_read",
     "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
     "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
 ]
@@ -60,10 +62,12 @@ class Stats(C.Structure):
     _fields_ = [("vcycles", C.c_longlong), ("solves", C.c_longlong), ("sweeps", C.c_longlong),
                 ("iters", C.c_longlong), ("steps", C.c_longlong), ("notconv", C.c_int),
                 ("residual", C.c_double), ("mg_residual", C.c_double), ("seconds", C.c_double),
-                ("bytes", C.c_double)]
+                ("bytes", C.c_double), ("vcycles_level", C.c_longlong * 2)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_}
+        d["vcycles_level"] = list(self.vcycles_level)
+        return d
 
 
 class ServerConfig(C.Structure):
@@ -113,6 +117,11 @@ def load():
     L.heat3d_fas_restrict.argtypes = [V, I, I]
     L.heat3d_fas_interpolate.argtypes = [V, I, I]
     L.pfasst_run.argtypes = [V, V, V, P(Stats)]
+    L.heat3d_set_interval.argtypes = [V, D, D]
+    L.heat3d_kernel_launches.argtypes = []
+    L.heat3d_kernel_launches.restype = C.c_longlong
+    L.heat3d_profile.argtypes = [V, I]
+    L.heat3d_profile_read.argtypes = [V, P(D), P(C.c_longlong), P(D), P(D), P(D)]
     if hasattr(L, "heat3d_server_create"):
         L.heat3d_server_create.argtypes = [P(ServerConfig), P(V)]
         L.heat3d_submit.argtypes = [V, P(Request), P(C.c_uint64)]
@@ -260,3 +269,24 @@ def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2,
     cfg.precision, cfg.forcing, cfg.batch, cfg.device = precision, forcing, batch, device
     cfg.use_graphs = use_graphs
     return cfg
+
+
+def heat3d_set_interval(ctx: Context, t0, T):
+    return _check(load().heat3d_set_interval(ctx.h, float(t0), float(T)), ctx.h)
+
+
+def heat3d_kernel_launches() -> int:
+    return int(load().heat3d_kernel_launches())
+
+
+def heat3d_profile(ctx: Context, kernel_class):
+    return _check(load().heat3d_profile(ctx.h, int(kernel_class)), ctx.h)
+
+
+def heat3d_profile_read(ctx: Context) -> dict:
+    ms, b, dp, fl = C.c_double(), C.c_double(), C.c_double(), C.c_double()
+    n = C.c_longlong()
+    _check(load().heat3d_profile_read(ctx.h, C.byref(ms), C.byref(n), C.byref(b), C.byref(dp),
+                                      C.byref(fl)), ctx.h)
+    return {"ms": ms.value, "launches": n.value, "bytes": b.value, "dp_ops": dp.value,
+            "flops": fl.value}
