@@ -194,6 +194,30 @@ int heat3d_profile_read(heat3d_ctx* ctx, double* ms, long long* launches, double
                         double* dp_ops, double* flops);
 
 /* ---------------------------------------------------------------------- */
+/* Solve without any device allocation (no counterpart in the paper).       */
+/* ---------------------------------------------------------------------- */
+
+/* mg_vcycle for callers that cannot allocate device memory (a framework that
+ * owns all device memory, a plugin given only its input and output buffers,
+ * a loop with a memory budget fixed in advance): solves (I - c Delta_h) u =
+ * rhs on an N^3 grid exactly as mg_vcycle does, with all scratch taken from a
+ * static device array of 32 MiB inside this library (held on every GPU that
+ * loads it until exit); no cudaMalloc, cudaFree or other allocating call.
+ *  - N = 2^k - 1 <= 63; larger N returns HEAT3D_EINVAL.  order 2 or 4;
+ *    precision HEAT3D_FP64 or HEAT3D_MIXED; c, max_cycles, tol as mg_vcycle.
+ *  - rhs, u: host or device, dense N^3 FP64; u is the warm start and result.
+ *  - Runs on the current device and `stream`, and returns with u complete.
+ *  - The first call on a device looks up the array's device address and sets
+ *    up the solver state: make it before any stream capture.
+ *  - Calls share the array (it keeps the last call's contents; the solver
+ *    clears what must start at zero).  Calls that overlap on the GPU race:
+ *    serialise them.  stats->seconds is not measured (0). */
+int mg_vcycle_noalloc(int N, int order, int precision, double c, const double* rhs, double* u,
+                      int max_cycles, double tol, void* stream, heat3d_stats* stats);
+/* Message of the last mg_vcycle_noalloc failure. */
+const char* mg_vcycle_noalloc_last_error(void);
+
+/* ---------------------------------------------------------------------- */
 /* Serving: continuous batching of independent heat-equation solves.        */
 /* ---------------------------------------------------------------------- */
 

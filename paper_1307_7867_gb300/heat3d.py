@@ -30,6 +30,7 @@ ABI_FUNCTIONS = [
     "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
     "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
     "heat3d_set_interval", "heat3d_kernel_launches", "heat3d_profile", "heat3d_profile_read",
+    "mg_vcycle_noalloc", "mg_vcycle_noalloc_last_error",
     "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
     "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
 ]
@@ -122,6 +123,9 @@ def load():
     L.heat3d_kernel_launches.restype = C.c_longlong
     L.heat3d_profile.argtypes = [V, I]
     L.heat3d_profile_read.argtypes = [V, P(D), P(C.c_longlong), P(D), P(D), P(D)]
+    L.mg_vcycle_noalloc.argtypes = [I, I, I, D, V, V, I, D, V, P(Stats)]
+    L.mg_vcycle_noalloc_last_error.argtypes = []
+    L.mg_vcycle_noalloc_last_error.restype = C.c_char_p
     if hasattr(L, "heat3d_server_create"):
         L.heat3d_server_create.argtypes = [P(ServerConfig), P(V)]
         L.heat3d_submit.argtypes = [V, P(Request), P(C.c_uint64)]
@@ -290,3 +294,17 @@ def heat3d_profile_read(ctx: Context) -> dict:
                                       C.byref(fl)), ctx.h)
     return {"ms": ms.value, "launches": n.value, "bytes": b.value, "dp_ops": dp.value,
             "flops": fl.value}
+
+
+def mg_vcycle_noalloc(N, order, precision, c, rhs, u, max_cycles, tol, stream=None,
+                      allow_notconv=False):
+    """mg_vcycle without device allocation (static scratch inside the library, N <= 63)."""
+    st = Stats()
+    sp = None
+    if stream is not None:
+        sp = C.c_void_p(stream.cuda_stream)
+    rc = load().mg_vcycle_noalloc(int(N), int(order), int(precision), float(c), _ptr(rhs), _ptr(u),
+                                  int(max_cycles), float(tol), sp, C.byref(st))
+    if rc != OK and not (allow_notconv and rc == ENOTCONV):
+        raise Heat3DError(rc, load().mg_vcycle_noalloc_last_error().decode())
+    return rc, st.as_dict()
