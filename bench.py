@@ -37,8 +37,8 @@ import numpy as np  # noqa: E402
 # Fine-level V-cycles per MLSDC step of the default workload, counted on a
 # full GB300 run (the oracle performs the same cycles: the parity tests check
 # equal counts).  Used only by --impl reference to scale its timed sample.
-REF_FINE_VCYCLES_PER_STEP = 240.0
-REF_COARSE_VCYCLES_PER_STEP = 40.0
+REF_FINE_VCYCLES_PER_STEP = 596.0
+REF_COARSE_VCYCLES_PER_STEP = 164.0
 
 WORKLOADS = {
     "c2": dict(
@@ -130,13 +130,14 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
-def make_cfg(H, w, precision=None, slices=None):
+def make_cfg(H, w, precision=None, slices=None, graphs=True):
     prec = H.MIXED if (precision or w["precision"]) == "mixed" else H.FP64
     return H.make_config(w["fine"], w["coarse"], dt=w["dt"], T=w["dt"],
                          sweeps_fine=w["sweeps_fine"], sweeps_coarse=w["sweeps_coarse"],
                          slices=slices or w["slices"], iters=w["iters"], tol_sdc=w["tol_sdc"],
                          mg_tol=w["mg_tol"], max_cycles=50, precision=prec,
-                         forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"])
+                         forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"],
+                         use_graphs=1 if graphs else 0, autotune=1)
 
 
 def peaks():
@@ -171,7 +172,7 @@ def run_ours(args, w, rank, world):
             dist.barrier()
         torch.cuda.synchronize()
 
-    ctx = H.Context(make_cfg(H, w))
+    ctx = H.Context(make_cfg(H, w, graphs=not args.no_graphs), stream=torch.cuda.Stream(dev))
     # warm-up steps (untimed)
     H.heat3d_set_interval(ctx, 0.0, W * dt)
     H.pfasst_run(ctx, u0_d, uT_d, allow_notconv=True)
@@ -332,6 +333,24 @@ def run_reference(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+def kernel_case(w, precision):
+    """Two fixed V(2,1) cycles of the workload's first fine substep solve: a small
+    launch sequence (a few dozen kernels) for kernel-level profiling."""
+    import torch
+    from paper_1307_7867_gb300 import build, heat3d as H, inputs
+    build.build()
+    Nf, order, M = w["fine"]
+    cfg = H.make_config((Nf, order, M), precision=H.MIXED if precision == "mixed" else H.FP64)
+    ctx = H.Context(cfg, stream=torch.cuda.Stream())
+    b = torch.from_numpy(inputs.sine_mode(Nf)).cuda()
+    u = torch.zeros_like(b)
+    c = w["dt"] * 0.1 * 0.17267316464601143  # dt * nu * tau_1 (5 Gauss-Lobatto nodes)
+    rc, st = H.mg_vcycle(ctx, 0, c, b, u, 2, -1.0)
+    torch.cuda.synchronize()
+    return {"kernel_case": precision, "N": Nf, "order": order, "vcycles": st["vcycles"],
+            "ms": st["seconds"] * 1e3, "mg_residual": st["mg_residual"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -341,6 +360,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
+    ap.add_argument("--kernel-case", choices=["fp64", "mixed"], default=None,
+                    help="profiling case: two fixed V(2,1) cycles of one fine-level solve only")
     args = ap.parse_args()
     w = WORKLOADS[args.workload]
     args.steps = args.steps or w["steps"]
@@ -349,6 +371,10 @@ def main():
         args.warmup = 3
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
+
+    if args.kernel_case:
+        print(json.dumps(kernel_case(w, args.kernel_case)), flush=True)
+        return
 
     if args.impl == "reference":
         if rank == 0:
@@ -364,7 +390,8 @@ def main():
         # the same workload with FP32 V-cycles inside FP64 refinement
         import torch
         from paper_1307_7867_gb300 import heat3d as H
-        cm = H.Context(make_cfg(H, w, precision="mixed"))
+        cm = H.Context(make_cfg(H, w, precision="mixed", graphs=not args.no_graphs),
+                       stream=torch.cuda.Stream())
         u0_d = torch.from_numpy(u0).cuda()
         o = torch.empty_like(u0_d)
         H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])

@@ -84,7 +84,10 @@ typedef struct {
   int batch;                /* state slots per level for sdc_sweep / serving (>= slices) */
   int device;               /* CUDA device ordinal */
   void* stream;             /* cudaStream_t for all work of this context (NULL: legacy) */
-  int use_graphs;           /* 1: replay V-cycles from captured CUDA graphs */
+  int use_graphs;           /* 1: replay each V-cycle from a captured CUDA graph (needs a
+                               non-default stream; ignored on the legacy stream) */
+  int autotune;             /* 1: time the stencil launch shapes of every multigrid level at
+                               heat3d_bind_workspace and keep the fastest (results identical) */
 } heat3d_config;
 
 typedef struct {

@@ -8,10 +8,13 @@
 
 namespace h3d {
 
-// z-marching launch shape: blocks of bx * by threads, each thread one (x, y)
-// column over zc consecutive planes.
+// Launch shape of the stencil kernels.
+// kind: 0 automatic (tiled for N >= 32, else z-march), 1 z-march (one column
+// per thread), 2 shared-memory tile 32 x 8 (128 threads), 3 tile 32 x 16 (256
+// threads); zc: planes per block along z.
 struct Shape {
-  int bx = 32, by = 4, zc = 16;
+  int kind = 0;
+  int zc = 16;
 };
 
 // Process-wide count of kernel launches (every launcher calls it once per launch).

@@ -88,6 +88,8 @@ int mg_vcycle_noalloc(int N, int order, int precision, double c, const double* r
     cfg.batch = 1;
     cfg.device = dev;
     cfg.stream = stream;
+    cfg.autotune = 0;    // tuning would create timing events
+    cfg.use_graphs = 0;  // graphs would be instantiated (a resource allocation)
     size_t need = 0;
     if (heat3d_workspace_size(&cfg, &need) != HEAT3D_OK || need > kNoAllocScratchBytes)
       return fail(HEAT3D_ENOMEM, "solver state does not fit in the no-allocation scratch array");

@@ -54,24 +54,44 @@ int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...) {
 namespace h3d {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+long long launches_total() { return g_launches.load(); }
+void launches_adjust(long long delta) { g_launches.fetch_add(delta); }
 }  // namespace h3d
 
+// Event pair around one launch of the profiled kernel class.  While a
+// V-cycle graph is being captured the pair belongs to that graph (and is read
+// after each replay); otherwise it comes from the context's pool.
 int h3d_prof_begin(heat3d_ctx* c, int cls) {
   if (c->prof_class == 0 || c->prof_class != cls) return -1;
-  if (c->prof_used * 2 + 2 > c->prof_ev.size()) {
+  std::vector<cudaEvent_t>& pool = c->capturing ? c->capturing->ev : c->prof_ev;
+  size_t used = c->capturing ? pool.size() / 2 : c->prof_used;
+  if (used * 2 + 2 > pool.size()) {
     for (int k = 0; k < 2; ++k) {
       cudaEvent_t e;
       if (cudaEventCreate(&e) != cudaSuccess) return -1;
-      c->prof_ev.push_back(e);
+      pool.push_back(e);
     }
   }
-  int pair = (int)c->prof_used++;
-  cudaEventRecord(c->prof_ev[2 * pair], c->st);
+  int pair = (int)used;
+  if (!c->capturing) c->prof_used++;
+  // inside a capture only an external record becomes an event-record node
+  if (c->capturing) cudaEventRecordWithFlags(pool[2 * pair], c->st, cudaEventRecordExternal);
+  else cudaEventRecord(pool[2 * pair], c->st);
   return pair;
 }
 
 void h3d_prof_end(heat3d_ctx* c, int pair, double bytes, double dpops, double flops) {
   if (pair < 0) return;
+  if (c->capturing) {
+    h3d::CycleGraph* g = c->capturing;
+    cudaEventRecordWithFlags(g->ev[2 * pair + 1], c->st, cudaEventRecordExternal);
+    g->prof_bytes += bytes;
+    g->prof_dpops += dpops;
+    g->prof_flops += flops;
+    g->prof_launches += 1;
+    return;
+  }
   cudaEventRecord(c->prof_ev[2 * pair + 1], c->st);
   c->prof_bytes += bytes;
   c->prof_dpops += dpops;
@@ -84,6 +104,7 @@ static void prof_harvest(heat3d_ctx* c) {
   for (size_t p = 0; p < c->prof_used; ++p) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->prof_ev[2 * p], c->prof_ev[2 * p + 1]) == cudaSuccess) c->prof_ms += ms;
+    else cudaGetLastError();
   }
   c->prof_used = 0;
 }
@@ -444,7 +465,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   T* oth = t;
   for (int s = 1; s < nu1; ++s) {
     int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
-    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
       jacobi_cost<T>(order, false, &cb, &cd, &cfl);
@@ -453,7 +474,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
     c->bytes += 3.0 * ts * pts;
     std::swap(cur, oth);
   }
-  CK(launch_resid<T>(order, g, B, cur, b, oth, cf, act, c->shape, st));
+  CK(launch_resid<T>(order, g, B, cur, b, oth, cf, act, L.shapeT[k], st));
   CK(launch_restrict<T>(g, L.mg[k + 1], B, oth, mgbuf<T>(L, k + 1, 0, b0), act, st));
   c->bytes += 3.0 * ts * pts + ts * pts * (1.0 + 1.0 / 8.0);
   T* ce = nullptr;
@@ -463,8 +484,8 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   for (int s = 0; s < nu2; ++s) {
     const bool upd = k == 0 && s == nu2 - 1;
     int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
-    if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, c->shape, st));
-    else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, c->shape, st));
+    if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, L.shapeT[k], st));
+    else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
       jacobi_cost<T>(order, upd, &cb, &cd, &cfl);
@@ -506,6 +527,85 @@ static int read_norms(heat3d_ctx* c, SdcLevel& L, int b0, int B, std::vector<dou
 // Solve (I - c_b Delta_h) u_b = rhs_b for items [b0, b0 + B) of level lev, u
 // warm-started and updated in place (item strides us, bs).  Coefficients of
 // slot `slot` must be set.  Returns ENOTCONV / ENAN per the tolerance rule.
+// ---- CUDA graphs of one V-cycle + refinement residual ----
+
+static bool graphs_usable(heat3d_ctx* c) {
+  return c->cfg.use_graphs && c->st != nullptr && c->st != cudaStreamLegacy &&
+         c->st != cudaStreamPerThread;
+}
+
+static CycleGraph* find_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* u,
+                              const double* rhs) {
+  for (CycleGraph* g : c->graphs)
+    if (g->lev == lev && g->slot == slot && g->b0 == b0 && g->B == B && g->u == u && g->rhs == rhs)
+      return g;
+  return nullptr;
+}
+
+static void free_graph(CycleGraph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+}
+
+static void drop_graph(heat3d_ctx* c, CycleGraph* g) {
+  c->graphs.erase(std::find(c->graphs.begin(), c->graphs.end(), g));
+  free_graph(g);
+}
+
+// Adds the profiled launches of one completed replay.
+static void graph_harvest(heat3d_ctx* c, CycleGraph* g) {
+  for (size_t p = 0; p + 1 < g->ev.size(); p += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g->ev[p], g->ev[p + 1]) == cudaSuccess) c->prof_ms += ms;
+    else cudaGetLastError();  // a failed timing read must not fail the next launch
+  }
+  c->prof_bytes += g->prof_bytes;
+  c->prof_dpops += g->prof_dpops;
+  c->prof_flops += g->prof_flops;
+  c->prof_launches += g->prof_launches;
+}
+
+// Captures fn() (the kernels of one cycle) into a new graph for this key.  The
+// launches and bytes it enqueues are recorded per replay instead of now.
+template <typename Fn>
+static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* u,
+                         const double* rhs, Fn& fn, CycleGraph** out) {
+  CycleGraph* g = new CycleGraph();
+  g->lev = lev; g->slot = slot; g->b0 = b0; g->B = B; g->u = u; g->rhs = rhs;
+  g->prof_class = c->prof_class;
+  const long long l0 = h3d::launches_total();
+  const double by0 = c->bytes;
+  cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    delete g;
+    return h3d_fail(c, HEAT3D_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+  }
+  c->capturing = g;
+  int rc = fn();
+  c->capturing = nullptr;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(c->st, &graph);
+  g->launches = h3d::launches_total() - l0;
+  h3d::launches_adjust(-g->launches);
+  g->bytes = c->bytes - by0;
+  c->bytes = by0;
+  if (rc < 0 || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    free_graph(g);
+    return rc < 0 ? rc : h3d_fail(c, HEAT3D_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&g->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    free_graph(g);
+    return h3d_fail(c, HEAT3D_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+  }
+  c->graphs.push_back(g);
+  *out = g;
+  return HEAT3D_OK;
+}
+
 template <typename T>
 static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
                       const double* rhs, long long bs, int max_cycles, double tol,
@@ -527,7 +627,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
   auto residual = [&]() -> int {
     CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
     int pr = lev == 0 ? h3d_prof_begin(c, HEAT3D_PROF_RESID64_FINE) : -1;
-    CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, c->shape, st));
+    CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, L.shape64, st));
     if (pr >= 0) {
       // neighbour sums + 2 FMAs (+ the FP64 e0 multiply when T is double)
       double dp = (order == 2 ? 7.0 : 13.0) + (sizeof(T) == 8 ? 1.0 : 0.0);
@@ -547,15 +647,37 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     }
     if (live < B) CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   }
-  while (cycles < max_cycles && live > 0) {
+  auto one_cycle = [&]() -> int {
     T* dummy = nullptr;
     RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &dummy));
+    return residual();
+  };
+  CycleGraph* gph = nullptr;
+  if (graphs_usable(c)) {
+    gph = find_graph(c, lev, slot, b0, B, u, rhs);
+    if (gph && gph->prof_class != c->prof_class) {
+      drop_graph(c, gph);
+      gph = nullptr;
+    }
+    if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, one_cycle, &gph));
+  }
+  while (cycles < max_cycles && live > 0) {
+    if (gph) {
+      CK(cudaGraphLaunch(gph->exec, st));
+      h3d::launches_adjust(gph->launches);
+      c->bytes += gph->bytes;
+      if (!gph->ev.empty()) {
+        CK(cudaStreamSynchronize(st));
+        graph_harvest(c, gph);
+      }
+    } else {
+      RET(one_cycle());
+    }
     ++cycles;
     if (s) {
       s->vcycles += live;
       s->vcycles_level[lev] += live;
     }
-    RET(residual());
     if (!fixed) {
       RET(read_norms(c, L, b0, B, nrm));
       bool changed = false;
@@ -605,7 +727,7 @@ int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B) {
   const int M = L.L.M;
   const long long fs = L.g.fs;
   CK(launch_lap(L.L.order, L.g, B * M, L.U + (size_t)b0 * M * fs, fs, L.F + (size_t)b0 * M * fs, fs,
-                L.alpha_nodes + (size_t)b0 * M, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+                L.alpha_nodes + (size_t)b0 * M, nullptr, nullptr, 0, nullptr, c->lv[lev].shape64, c->st));
   c->bytes += 16.0 * L.L.N * L.L.N * (double)L.L.N * B * M;
   return HEAT3D_OK;
 }
@@ -671,7 +793,7 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
     CK(launch_lap(L.L.order, L.g, B, U + (size_t)(m + 1) * fs, (long long)M * fs,
                   F + (size_t)(m + 1) * fs, (long long)M * fs, L.alpha_items + b0,
                   add ? I + (size_t)(m + 1) * fs : nullptr, add ? I + (size_t)(m + 1) * fs : nullptr,
-                  (long long)(M - 1) * fs, nullptr, c->shape, st));
+                  (long long)(M - 1) * fs, nullptr, L.shape64, st));
     c->bytes += pts * (16.0 + (add ? 16.0 : 0.0));
   }
   if (s) s->sweeps += 1;
@@ -691,7 +813,7 @@ int h3d_fas_restrict(heat3d_ctx* c, int b0, int B) {
                        G.U + (size_t)b0 * MG * gf, G.UGr + (size_t)b0 * MG * gf,
                        G.qF + (size_t)b0 * MG * gf, F.items_d + b0, c->map_d, F.phi, st));
   CK(launch_lap(G.L.order, G.g, B * MG, G.U + (size_t)b0 * MG * gf, gf, G.F + (size_t)b0 * MG * gf, gf,
-                G.alpha_nodes + (size_t)b0 * MG, nullptr, nullptr, 0, nullptr, c->shape, st));
+                G.alpha_nodes + (size_t)b0 * MG, nullptr, nullptr, 0, nullptr, G.shape64, st));
   CK(launch_fas_tau(MG, G.g, B, G.qF + (size_t)b0 * MG * gf, G.F + (size_t)b0 * MG * gf,
                     G.tauS + (size_t)b0 * (MG - 1) * gf, G.items_d + b0, G.phi, st));
   G.has_tau = true;
@@ -745,7 +867,7 @@ static int coarse_pass(heat3d_ctx* c, int P, heat3d_stats* s) {
     if (p > 0) {
       CK(launch_copy(G.g, 1, G.U + ((size_t)(p - 1) * MG + MG - 1) * gf, 0, G.U + (size_t)p * MG * gf, 0, c->st));
       CK(launch_lap(G.L.order, G.g, 1, G.U + (size_t)p * MG * gf, 0, G.F + (size_t)p * MG * gf, 0,
-                    G.alpha_items + p, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+                    G.alpha_items + p, nullptr, nullptr, 0, nullptr, G.shape64, c->st));
     }
     for (int k = 0; k < c->cfg.sweeps_coarse; ++k) {
       int rc = h3d_sweep(c, 1, p, 1, -1.0, s);
@@ -765,7 +887,7 @@ static int forward_fine(heat3d_ctx* c, int P) {
   CK(launch_copy(F.g, P - 1, F.U + (size_t)(MF - 1) * ff, (long long)MF * ff, F.U + (size_t)MF * ff,
                  (long long)MF * ff, c->st));
   CK(launch_lap(F.L.order, F.g, P - 1, F.U + (size_t)MF * ff, (long long)MF * ff, F.F + (size_t)MF * ff,
-                (long long)MF * ff, F.alpha_items + 1, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+                (long long)MF * ff, F.alpha_items + 1, nullptr, nullptr, 0, nullptr, F.shape64, c->st));
   return HEAT3D_OK;
 }
 
@@ -843,6 +965,86 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
 }
 
 // ---------------------------------------------------------------------------
+// autotuner: launch shape per multigrid level (all shapes give identical results)
+// ---------------------------------------------------------------------------
+
+template <typename Launch>
+static float time_shape(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1, Launch&& launch) {
+  if (launch() != cudaSuccess) return 1e30f;  // warm-up
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, c->st);
+    cudaError_t e = launch();
+    cudaEventRecord(e1, c->st);
+    if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    best = std::min(best, ms);
+  }
+  return best;
+}
+
+static std::vector<Shape> shape_candidates(int N) {
+  std::vector<Shape> v;
+  if (N < 8) {
+    v.push_back(Shape{1, N});
+    return v;
+  }
+  for (int kind = 1; kind <= 3; ++kind)
+    for (int zc : {4, 8, 16, 32, 64})
+      if (zc <= N) v.push_back(Shape{kind, zc});
+  return v;
+}
+
+template <typename T>
+static int autotune_T(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1) {
+  for (int lev = 0; lev < c->cfg.nlevels; ++lev) {
+    SdcLevel& L = c->lv[lev];
+    for (int k = 0; k < L.nmg; ++k) {
+      const Grid& g = L.mg[k];
+      const Coef<T>* cf = coefT<T>(L, 0, k, 0);
+      T* b = mgbuf<T>(L, k, 0, 0);
+      T* e = mgbuf<T>(L, k, 1, 0);
+      T* t = mgbuf<T>(L, k, 2, 0);
+      float best = 1e30f;
+      Shape pick{1, std::min(16, g.N)};
+      for (Shape sh : shape_candidates(g.N)) {
+        float ms = time_shape(c, e0, e1, [&] {
+          return launch_jacobi<T>(L.L.order, g, L.B, e, b, t, nullptr, 0, cf, nullptr, sh, c->st);
+        });
+        if (ms < best) { best = ms; pick = sh; }
+      }
+      L.shapeT[k] = pick;
+    }
+    float best = 1e30f;
+    Shape pick{1, std::min(16, L.g.N)};
+    const long long fs = L.g.fs;
+    for (Shape sh : shape_candidates(L.g.N)) {
+      float ms = time_shape(c, e0, e1, [&] {
+        return launch_lap(L.L.order, L.g, L.B, L.U, (long long)L.L.M * fs, L.F, (long long)L.L.M * fs,
+                          L.alpha_items, nullptr, nullptr, 0, nullptr, sh, c->st);
+      });
+      if (ms < best) { best = ms; pick = sh; }
+    }
+    L.shape64 = pick;
+  }
+  return HEAT3D_OK;
+}
+
+int h3d_autotune(heat3d_ctx* c) {
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const long long l0 = h3d::launches_total();
+  int rc = h3d_tsize(c) == 4 ? autotune_T<float>(c, e0, e1) : autotune_T<double>(c, e0, e1);
+  h3d::launches_adjust(-(h3d::launches_total() - l0));  // tuning launches are not work
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaStreamSynchronize(c->st));
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 
@@ -911,6 +1113,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->device = 0;
   cfg->stream = nullptr;
   cfg->use_graphs = 0;
+  cfg->autotune = 1;
 }
 
 int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes) {
@@ -963,6 +1166,7 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->st));
   c->bound = true;
+  if (c->cfg.autotune) RET(h3d_autotune(c));
   return HEAT3D_OK;
 }
 
@@ -1000,6 +1204,8 @@ int heat3d_profile_read(heat3d_ctx* c, double* ms, long long* launches, double* 
 int heat3d_destroy(heat3d_ctx* c) {
   if (!c) return HEAT3D_EINVAL;
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  for (CycleGraph* g : c->graphs) free_graph(g);
+  c->graphs.clear();
   h3d_destroy_extras(c);
   delete c;
   return HEAT3D_OK;
@@ -1019,7 +1225,7 @@ int heat3d_apply_laplacian(heat3d_ctx* c, int level, const double* u, double* ou
   SdcLevel& L = c->lv[level];
   RET(h3d_load_dense(c, level, u, L.abi_u));
   CK(launch_lap(L.L.order, L.g, 1, L.abi_u, 0, L.abi_p0, 0, L.alpha_items, nullptr, nullptr, 0,
-                nullptr, c->shape, c->st));
+                nullptr, L.shape64, c->st));
   RET(h3d_store_dense(c, level, L.abi_p0, out));
   return HEAT3D_OK;
 }
@@ -1091,7 +1297,7 @@ int heat3d_set_node(heat3d_ctx* c, int level, int item, int node, const double* 
   double* dst = L.U + ((size_t)item * L.L.M + node) * L.g.fs;
   RET(h3d_load_dense(c, level, in, dst));
   CK(launch_lap(L.L.order, L.g, 1, dst, 0, L.F + ((size_t)item * L.L.M + node) * L.g.fs, 0,
-                L.alpha_items + item, nullptr, nullptr, 0, nullptr, c->shape, c->st));
+                L.alpha_items + item, nullptr, nullptr, 0, nullptr, L.shape64, c->st));
   CK(cudaStreamSynchronize(c->st));
   return HEAT3D_OK;
 }

@@ -45,6 +45,25 @@ struct SdcLevel {
   std::vector<ItemSDC> items_h;
   std::vector<double> t0, nu, dt;
   bool has_tau = false;
+  // launch shapes: multigrid kernels of level k in the solve precision, and
+  // the FP64 kernels (operator, refinement residual) on the level's grid
+  Shape shapeT[kMaxLevels];
+  Shape shape64;
+};
+
+// A captured V-cycle (+ norm reset + refinement residual) for one solve key.
+struct CycleGraph {
+  int lev = 0, slot = 0, b0 = 0, B = 0;
+  const double* u = nullptr;
+  const double* rhs = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels per replay
+  double bytes = 0.0;      // algorithmic bytes per replay
+  // profiling of the captured kernel class: event pairs owned by this graph
+  int prof_class = 0;
+  std::vector<cudaEvent_t> ev;
+  double prof_bytes = 0.0, prof_dpops = 0.0, prof_flops = 0.0;
+  long long prof_launches = 0;
 };
 
 }  // namespace h3d
@@ -68,6 +87,10 @@ struct heat3d_ctx {
   size_t prof_used = 0;              // pairs recorded and not yet harvested
   double prof_ms = 0.0, prof_bytes = 0.0, prof_dpops = 0.0, prof_flops = 0.0;
   long long prof_launches = 0;
+  // CUDA graphs of V-cycles (cfg.use_graphs); `capturing` routes profiling
+  // events into the graph being captured
+  std::vector<h3d::CycleGraph*> graphs;
+  h3d::CycleGraph* capturing = nullptr;
 };
 
 // Event bracketing for the profiled kernel class: returns a pair index or -1.
@@ -92,3 +115,8 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s);
 int h3d_load_dense(heat3d_ctx* c, int lev, const double* src, double* dst_pitched);
 int h3d_store_dense(heat3d_ctx* c, int lev, const double* src_pitched, double* dst);
 void h3d_destroy_extras(heat3d_ctx* c);
+int h3d_autotune(heat3d_ctx* c);
+namespace h3d {
+long long launches_total();
+void launches_adjust(long long delta);
+}

@@ -1,0 +1,438 @@
+// stencil_kernels.cu -- the 7-point and 13-point (wide) stencil kernels of the
+// spatial operator (Sec. 1, method of lines) and of the multigrid smoother and
+// residuals (Sec. 1.2), templated on the storage type and stencil order.
+//
+// Two drivers share one operator interface:
+//  * k_tile (grids with N >= 32): a block owns a 32 x TY tile of x-y points
+//    and marches along z through a chunk of planes.  The planes it needs
+//    (z-R .. z+R, R = 1 or 2) live in a shared-memory ring that cp.async
+//    fills D planes ahead in 16-byte chunks, so HBM streams while the block
+//    computes; every neighbour is read from shared memory and each thread
+//    computes RY rows (independent FP64 chains for the FP64 pipe).  Cells of
+//    the tile halo that fall outside the domain are written with plain loads
+//    under the boundary rule.
+//  * k_zmarch (small grids): one (x, y) column per thread, z-neighbours in a
+//    register queue, x/y neighbours through L1.
+// Boundary rule of every stencil read: indices -1 and N are the Dirichlet
+// zeros; the wide stencil's ghosts -2 and N+1 are -u(0) and -u(N-1) (odd
+// reflection).
+//
+// Operator interface: src(b) is the field whose stencil is taken, init(b)
+// loads per-item coefficients, load(b, idx) the per-point extra operands
+// (issued before the plane barrier), apply(b, idx, u, s1, s2, ex) produces the
+// outputs from the centre u, the sum s1 of the 6 nearest and s2 of the 6
+// second neighbours, and returns the value whose max |.| is accumulated when
+// the launch asks for a norm.
+#include "kernels.cuh"
+
+namespace h3d {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T* p) { return __ldg(p); }
+
+// Value at (i, j, k) under the boundary rule, for indices in [-2, N+1].
+template <typename T>
+__device__ __forceinline__ T at(const T* __restrict__ u, const Grid& g, int i, int j, int k) {
+  const int N = g.N;
+  bool neg = false;
+  if (i < 0 || i >= N) {
+    if (i == -1 || i == N) return T(0);
+    neg = !neg;
+    i = i < 0 ? 0 : N - 1;
+  }
+  if (j < 0 || j >= N) {
+    if (j == -1 || j == N) return T(0);
+    neg = !neg;
+    j = j < 0 ? 0 : N - 1;
+  }
+  if (k < 0 || k >= N) {
+    if (k == -1 || k == N) return T(0);
+    neg = !neg;
+    k = k < 0 ? 0 : N - 1;
+  }
+  T v = ldg(u + (long long)k * g.plane + (long long)j * g.px + i);
+  return neg ? -v : v;
+}
+
+// As at(), and 0 for indices beyond the ghost layer (never used by a stencil).
+template <typename T>
+__device__ __forceinline__ T at_any(const T* __restrict__ u, const Grid& g, int i, int j, int k) {
+  const int N = g.N;
+  if (i < -2 || i > N + 1 || j < -2 || j > N + 1 || k < -2 || k > N + 1) return T(0);
+  return at(u, g, i, j, k);
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+__device__ __forceinline__ void warp_max_to(unsigned long long v, unsigned long long* dst) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(dst, v);
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int n>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+template <typename T, int ORDER>
+__device__ __forceinline__ T combine(T s1, T s2) {
+  if (ORDER == 2) return s1;
+  return fma(T(16), s1, -s2);
+}
+
+// ---------------------------------------------------------------------------
+// operators
+// ---------------------------------------------------------------------------
+
+// F = alpha_b L u (and the next substep's rhs add_dst = u + add_src).
+template <int ORDER>
+struct OpLap {
+  using T = double;
+  struct Ex { double add; };
+  const double* u; long long us;
+  double* out; long long os;
+  const double* alpha;
+  const double* add_src; double* add_dst; long long as;
+  double a;
+  __device__ const double* src(int b) const { return u + b * us; }
+  __device__ void init(int b) { a = alpha[b]; }
+  __device__ Ex load(int b, long long idx) const {
+    return Ex{add_src ? add_src[b * as + idx] : 0.0};
+  }
+  __device__ double apply(int b, long long idx, double c, double s1, double s2, const Ex& ex) {
+    double L = ORDER == 2 ? fma(-6.0, c, s1) : fma(-90.0, c, fma(16.0, s1, -s2));
+    out[b * os + idx] = a * L;
+    if (add_src) add_dst[b * as + idx] = c + ex.add;
+    return 0.0;
+  }
+};
+
+// r = b - A u in FP64, stored as TR; e0 = wd r (first Jacobi iterate from zero).
+template <int ORDER, typename TR>
+struct OpResid64 {
+  using T = double;
+  struct Ex { double b; };
+  const double* u; long long us;
+  const double* bb; long long bs;
+  const Coef<double>* coef;
+  TR* r; TR* e0; const Coef<TR>* coef_r; long long rs;
+  double d, e; TR wd;
+  __device__ const double* src(int b) const { return u + b * us; }
+  __device__ void init(int b) {
+    d = coef[b].d;
+    e = coef[b].e;
+    wd = e0 ? coef_r[b].wd : TR(0);
+  }
+  __device__ Ex load(int b, long long idx) const { return Ex{bb[b * bs + idx]}; }
+  __device__ double apply(int b, long long idx, double c, double s1, double s2, const Ex& ex) {
+    double S = combine<double, ORDER>(s1, s2);
+    double res = fma(-d, c, fma(e, S, ex.b));
+    TR rt = (TR)res;
+    r[b * rs + idx] = rt;
+    if (e0) e0[b * rs + idx] = wd * rt;
+    return res;
+  }
+};
+
+// Damped Jacobi on the error equation: v = e + wd (r - A e); stored, or added to u64.
+template <typename TT, int ORDER>
+struct OpJacobi {
+  using T = TT;
+  struct Ex { T r; double u; };
+  const T* e; const T* r; T* out; long long fs;
+  double* u64; long long u64s;
+  const Coef<T>* coef;
+  T d, ec, wd;
+  __device__ const T* src(int b) const { return e + b * fs; }
+  __device__ void init(int b) { d = coef[b].d; ec = coef[b].e; wd = coef[b].wd; }
+  __device__ Ex load(int b, long long idx) const {
+    return Ex{r[b * fs + idx], u64 ? u64[b * u64s + idx] : 0.0};
+  }
+  __device__ double apply(int b, long long idx, T c, T s1, T s2, const Ex& ex) {
+    T S = combine<T, ORDER>(s1, s2);
+    T res = fma(-d, c, fma(ec, S, ex.r));
+    T v = fma(wd, res, c);
+    if (u64) u64[b * u64s + idx] = ex.u + (double)v;
+    else out[b * fs + idx] = v;
+    return 0.0;
+  }
+};
+
+// rr = r - A e
+template <typename TT, int ORDER>
+struct OpResid {
+  using T = TT;
+  struct Ex { T r; };
+  const T* e; const T* r; T* rr; long long fs;
+  const Coef<T>* coef;
+  T d, ec;
+  __device__ const T* src(int b) const { return e + b * fs; }
+  __device__ void init(int b) { d = coef[b].d; ec = coef[b].e; }
+  __device__ Ex load(int b, long long idx) const { return Ex{r[b * fs + idx]}; }
+  __device__ double apply(int b, long long idx, T c, T s1, T s2, const Ex& ex) {
+    T S = combine<T, ORDER>(s1, s2);
+    rr[b * fs + idx] = fma(-d, c, fma(ec, S, ex.r));
+    return 0.0;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// drivers
+// ---------------------------------------------------------------------------
+
+template <int ORDER, bool NORM, typename Op>
+__global__ void __launch_bounds__(128) k_zmarch(Grid g, int nzc, int zc, const int* active,
+                                                unsigned long long* norm_bits, Op op) {
+  using T = typename Op::T;
+  constexpr int R = ORDER == 2 ? 1 : 2;
+  const int b = blockIdx.z / nzc;
+  if (active && !active[b]) return;  // uniform over the block
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int z0 = (blockIdx.z - b * nzc) * zc;
+  const int z1 = min(g.N, z0 + zc);
+  unsigned long long mx = 0ull;
+  if (i < g.N && j < g.N) {
+    Op o = op;
+    o.init(b);
+    const T* __restrict__ u = o.src(b);
+    T q[2 * R + 1];
+#pragma unroll
+    for (int d = -R; d <= R; ++d) q[R + d] = at(u, g, i, j, z0 + d);
+    for (int k = z0; k < z1; ++k) {
+      const long long idx = (long long)k * g.plane + (long long)j * g.px + i;
+      typename Op::Ex ex = o.load(b, idx);
+      T s1 = ((at(u, g, i - 1, j, k) + at(u, g, i + 1, j, k)) +
+              (at(u, g, i, j - 1, k) + at(u, g, i, j + 1, k))) + (q[R - 1] + q[R + 1]);
+      T s2 = T(0);
+      if (R == 2)
+        s2 = ((at(u, g, i - 2, j, k) + at(u, g, i + 2, j, k)) +
+              (at(u, g, i, j - 2, k) + at(u, g, i, j + 2, k))) + (q[0] + q[2 * R]);
+      double rv = o.apply(b, idx, q[R], s1, s2, ex);
+      if (NORM) {
+        unsigned long long bits = abs_bits(rv);
+        mx = bits > mx ? bits : mx;
+      }
+#pragma unroll
+      for (int d = 0; d < 2 * R; ++d) q[d] = q[d + 1];
+      if (k + 1 < z1) q[2 * R] = at(u, g, i, j, k + R + 1);
+    }
+  }
+  if (NORM) warp_max_to(mx, norm_bits + b);
+}
+
+template <typename T>
+__host__ __device__ constexpr int halo_x() { return 16 / (int)sizeof(T); }
+
+template <typename T, int ORDER, int TYT, int RY, int D>
+constexpr int tile_smem_bytes() {
+  return (2 * (ORDER == 2 ? 1 : 2) + D) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) *
+         (32 + 2 * halo_x<T>()) * (int)sizeof(T);
+}
+
+template <int ORDER, int TYT, int RY, int D, bool NORM, typename Op>
+__global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, const int* active,
+                                                   unsigned long long* norm_bits, Op op) {
+  using T = typename Op::T;
+  constexpr int R = ORDER == 2 ? 1 : 2;
+  constexpr int TX = 32, TY = TYT * RY;
+  constexpr int XH = halo_x<T>();
+  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D;
+  constexpr int CH = SX / XH;  // 16-byte chunks per shared row
+  constexpr int NT = 32 * TYT;
+  constexpr int PS = SY * SX;  // elements per shared plane
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  const int b = blockIdx.z / nzc;
+  if (active && !active[b]) return;  // uniform over the block
+  const int N = g.N;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = (blockIdx.z - b * nzc) * zc, z1 = min(N, z0 + zc);
+  Op o = op;
+  o.init(b);
+  const T* __restrict__ u = o.src(b);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+
+  // Plane z into its ring slot: interior 16-byte chunks by cp.async, the rest
+  // (domain halo, ghost planes) by plain loads under the boundary rule.
+  auto issue = [&](int z) {
+    if (z <= z1 - 1 + R) {
+      T* dst = ring + ((z - z0 + R) % NB) * PS;
+      const bool zin = z >= 0 && z < N;
+      for (int c = tid; c < SY * CH; c += NT) {
+        const int ry = c / CH, cx = c - ry * CH;
+        const int gy = y0 - R + ry, gx = x0 - XH + cx * XH;
+        T* d = dst + ry * SX + cx * XH;
+        if (zin && gy >= 0 && gy < N && gx >= 0 && gx + XH <= N) {
+          cp_async16(d, u + (long long)z * g.plane + (long long)gy * g.px + gx);
+        } else {
+#pragma unroll
+          for (int e = 0; e < XH; ++e) d[e] = at_any(u, g, gx + e, gy, z);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  for (int z = z0 - R; z < z0 + R + D; ++z) issue(z);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = x0 + tx;
+  unsigned long long mx = 0ull;
+  for (int k = z0; k < z1; ++k) {
+    typename Op::Ex ex[RY];
+    long long idx[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const int j = y0 + ty * RY + r;
+      idx[r] = (long long)k * g.plane + (long long)j * g.px + i;
+      if (i < N && j < N) ex[r] = o.load(b, idx[r]);
+    }
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    const int base = k - z0 + R;
+    const T* P0 = ring + (base % NB) * PS;
+    const T* Pm1 = ring + ((base - 1) % NB) * PS;
+    const T* Pp1 = ring + ((base + 1) % NB) * PS;
+    const T* Pm2 = ring + ((base + NB - 2) % NB) * PS;
+    const T* Pp2 = ring + ((base + 2) % NB) * PS;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const int j = y0 + ty * RY + r;
+      const int o0 = (R + ty * RY + r) * SX + XH + tx;
+      const T c = P0[o0];
+      T s1 = ((P0[o0 - 1] + P0[o0 + 1]) + (P0[o0 - SX] + P0[o0 + SX])) + (Pm1[o0] + Pp1[o0]);
+      T s2 = T(0);
+      if (R == 2)
+        s2 = ((P0[o0 - 2] + P0[o0 + 2]) + (P0[o0 - 2 * SX] + P0[o0 + 2 * SX])) + (Pm2[o0] + Pp2[o0]);
+      if (i < N && j < N) {
+        double rv = o.apply(b, idx[r], c, s1, s2, ex[r]);
+        if (NORM) {
+          unsigned long long bits = abs_bits(rv);
+          mx = bits > mx ? bits : mx;
+        }
+      }
+    }
+    __syncthreads();
+    issue(k + R + D);
+  }
+  cp_async_wait<0>();
+  if (NORM) warp_max_to(mx, norm_bits + b);
+}
+
+constexpr int kTileD = 2;
+
+template <int ORDER, bool NORM, typename Op>
+cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long long* norm_bits,
+                        const Op& op, Shape sh, cudaStream_t st) {
+  using T = typename Op::T;
+  if (B <= 0 || g.N <= 0) return cudaSuccess;
+  int kind = sh.kind;
+  if (kind == 0) kind = g.N >= 32 ? 3 : 1;
+  int zc = sh.zc > 0 ? sh.zc : 16;
+  if (zc > g.N) zc = g.N;
+  const int nzc = (g.N + zc - 1) / zc;
+  if (kind == 1) {
+    dim3 blk(32, 4, 1);
+    dim3 grd((g.N + 31) / 32, (g.N + 3) / 4, nzc * B);
+    k_zmarch<ORDER, NORM, Op><<<grd, blk, 0, st>>>(g, nzc, zc, active, norm_bits, op);
+  } else if (kind == 2) {
+    constexpr int TYT = 4, RY = 2;
+    dim3 blk(32, TYT, 1);
+    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
+    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
+        g, nzc, zc, active, norm_bits, op);
+  } else {
+    constexpr int TYT = 8, RY = 2;
+    dim3 blk(32, TYT, 1);
+    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
+    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
+        g, nzc, zc, active, norm_bits, op);
+  }
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long long u_stride,
+                       double* out, long long out_stride, const double* alpha,
+                       const double* add_src, double* add_dst, long long add_stride,
+                       const int* active, Shape sh, cudaStream_t st) {
+  if (order == 2) {
+    OpLap<2> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+    return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+  }
+  OpLap<4> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+  return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+}
+
+template <typename TR>
+cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, long long u_stride,
+                           const double* b, long long b_stride, const Coef<double>* coef,
+                           TR* r_out, TR* e0_out, const Coef<TR>* coef_r,
+                           unsigned long long* norm_bits, const int* active, Shape sh,
+                           cudaStream_t st) {
+  if (order == 2) {
+    OpResid64<2, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+    return norm_bits ? run_stencil<2, true>(g, B, active, norm_bits, op, sh, st)
+                     : run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+  }
+  OpResid64<4, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+  return norm_bits ? run_stencil<4, true>(g, B, active, norm_bits, op, sh, st)
+                   : run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+}
+
+template <typename T>
+cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
+                          double* u64, long long u64_stride, const Coef<T>* coef,
+                          const int* active, Shape sh, cudaStream_t st) {
+  if (order == 2) {
+    OpJacobi<T, 2> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+    return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+  }
+  OpJacobi<T, 4> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+  return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+}
+
+template <typename T>
+cudaError_t launch_resid(int order, const Grid& g, int B, const T* e, const T* r, T* rr,
+                         const Coef<T>* coef, const int* active, Shape sh, cudaStream_t st) {
+  if (order == 2) {
+    OpResid<T, 2> op{e, r, rr, g.fs, coef, T(0), T(0)};
+    return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+  }
+  OpResid<T, 4> op{e, r, rr, g.fs, coef, T(0), T(0)};
+  return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+}
+
+#define H3D_INST(T)                                                                            \
+  template cudaError_t launch_resid64<T>(int, const Grid&, int, const double*, long long,      \
+                                         const double*, long long, const Coef<double>*, T*, T*, \
+                                         const Coef<T>*, unsigned long long*, const int*, Shape, \
+                                         cudaStream_t);                                         \
+  template cudaError_t launch_jacobi<T>(int, const Grid&, int, const T*, const T*, T*, double*, \
+                                        long long, const Coef<T>*, const int*, Shape,          \
+                                        cudaStream_t);                                          \
+  template cudaError_t launch_resid<T>(int, const Grid&, int, const T*, const T*, T*,          \
+                                       const Coef<T>*, const int*, Shape, cudaStream_t);
+H3D_INST(double)
+H3D_INST(float)
+#undef H3D_INST
+
+}  // namespace h3d

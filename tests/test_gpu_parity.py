@@ -227,3 +227,45 @@ def test_run_mixed_precision_matches_fp64_oracle(H, oracle):
     ref, _, _ = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11), 1 / 32, 2, u0,
                                  nsweeps_fine=2, max_iters=20, tol=1e-10)
     assert rel(uT, ref) <= 1e-9
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graphs_and_autotune_change_nothing(H, oracle, precision):
+    """V-cycles replayed from CUDA graphs (private stream) and autotuned launch
+    shapes give bitwise the same MLSDC result as plain launches with the
+    default shapes; the FP64 run also matches the oracle."""
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    prec = H.FP64 if precision == "fp64" else H.MIXED
+    outs = []
+    for graphs, tune in ((0, 0), (1, 1), (1, 0)):
+        cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, precision=prec, mg_tol=1e-11,
+                            use_graphs=graphs, autotune=tune)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.sine_mode(31)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        outs.append((uT, st["vcycles"]))
+    for uT, v in outs[1:]:
+        assert np.array_equal(uT, outs[0][0]) and v == outs[0][1]
+    if precision == "fp64":
+        ref, _, _ = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11), 1 / 32, 2,
+                                     inputs.sine_mode(31), nsweeps_fine=2, max_iters=20, tol=1e-10)
+        assert rel(outs[1][0], ref) <= 1e-11
+
+
+def test_graph_replay_counts_launches_and_profile(H):
+    """Launch counter and the kernel profile include graph replays."""
+    N = 63
+    cfg = H.make_config((N, 4, 5), dt=1 / 16, T=1 / 16, sweeps_fine=1, tol_sdc=-1.0,
+                        use_graphs=1)
+    ctx = H.Context(cfg, stream=torch.cuda.Stream())
+    u0 = inputs.sine_mode(N)
+    uT = np.empty_like(u0)
+    H.pfasst_run(ctx, u0, uT)  # captures the graphs
+    H.heat3d_profile(ctx, H.PROF_JACOBI_FINE)
+    n0 = H.heat3d_kernel_launches()
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    n1 = H.heat3d_kernel_launches()
+    prof = H.heat3d_profile_read(ctx)
+    assert n1 - n0 > 10 * st["vcycles"]
+    assert prof["launches"] == 2 * st["vcycles"] and prof["ms"] > 0
