@@ -62,8 +62,10 @@ typedef struct {
 /* Multigrid settings for every implicit solve (Sec. 1.2). */
 typedef struct {
   int nu1, nu2;   /* damped-Jacobi pre- and post-smoothing sweeps (V(2,1)) */
-  int max_cycles; /* cap per solve */
+  int max_cycles; /* cap per solve, counted in refinement steps */
   double tol;     /* stop when max|b - A u| <= tol; tol < 0: exactly max_cycles cycles */
+  int inner;      /* V-cycles per refinement step (per FP64 residual), >= 1; the
+                     tolerance is checked after each step */
 } heat3d_mg;
 
 typedef struct {

@@ -436,7 +436,11 @@ static void jacobi_cost(int order, bool upd, double* bytes, double* dp, double* 
 
 template <typename T>
 static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int B,
-                        const int* act, double* u64, long long us, T** result) {
+                        const int* act, double* u64, long long us, T** result, bool warm = false,
+                        bool final = true) {
+  // Level 0 options: `warm` starts from the correction in *result (else from
+  // e_0 = wd r written by the residual kernel); `final` adds the correction to
+  // u64 in the last post-smoothing sweep (else *result returns its buffer).
   const bool prof_here = k == 0 && &L == &c->lv[0];
   const Grid& g = L.mg[k];
   const int order = L.L.order;
@@ -449,7 +453,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   const size_t ts = sizeof(T), pts = (size_t)g.N * g.N * g.N * B;
   if (g.N == 1) {
     CK(launch_jacobi_zero<T>(g, B, b, e, cf, true, act, st));
-    if (k == 0) {
+    if (k == 0 && final) {
       CK(launch_update<T>(g, B, e, u64, us, act, st));
       *result = nullptr;
     } else {
@@ -463,7 +467,13 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   }
   T* cur = e;
   T* oth = t;
-  for (int s = 1; s < nu1; ++s) {
+  int first = 1;
+  if (k == 0 && warm) {
+    cur = *result;
+    oth = cur == e ? t : e;
+    first = 0;
+  }
+  for (int s = first; s < nu1; ++s) {
     int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
     CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
@@ -482,7 +492,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   CK(launch_prolong_add<T>(L.mg[k + 1], g, B, ce, L.mg[k + 1].fs, cur, g.fs, act, st));
   c->bytes += ts * pts * (2.0 + 1.0 / 8.0);
   for (int s = 0; s < nu2; ++s) {
-    const bool upd = k == 0 && s == nu2 - 1;
+    const bool upd = k == 0 && final && s == nu2 - 1;
     int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
     if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, L.shapeT[k], st));
     else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
@@ -499,7 +509,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
     c->bytes += 3.0 * ts * pts;
     std::swap(cur, oth);
   }
-  if (k == 0) {
+  if (k == 0 && final) {
     CK(launch_update<T>(g, B, cur, u64, us, act, st));
     c->bytes += (ts + 16.0) * pts;
     *result = nullptr;
@@ -647,9 +657,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     }
     if (live < B) CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   }
+  const int inner = std::max(1, c->cfg.mg.inner);
   auto one_cycle = [&]() -> int {
-    T* dummy = nullptr;
-    RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &dummy));
+    T* cur = nullptr;
+    for (int q = 0; q < inner; ++q)
+      RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &cur, q > 0, q == inner - 1));
     return residual();
   };
   CycleGraph* gph = nullptr;
@@ -675,8 +687,8 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     }
     ++cycles;
     if (s) {
-      s->vcycles += live;
-      s->vcycles_level[lev] += live;
+      s->vcycles += (long long)live * inner;
+      s->vcycles_level[lev] += (long long)live * inner;
     }
     if (!fixed) {
       RET(read_norms(c, L, b0, B, nrm));
@@ -1106,7 +1118,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->iters = 20;
   cfg->tol_sdc = 1e-10;
   cfg->predictor = 1;
-  cfg->mg = heat3d_mg{2, 1, 50, 1e-10};
+  cfg->mg = heat3d_mg{2, 1, 50, 1e-10, 1};
   cfg->precision = HEAT3D_FP64;
   cfg->forcing = HEAT3D_FORCING_PAPER_LITERAL;
   cfg->batch = 1;

@@ -47,7 +47,8 @@ class Level(C.Structure):
 
 
 class MG(C.Structure):
-    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double)]
+    _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double),
+                ("inner", C.c_int)]
 
 
 class Config(C.Structure):
@@ -259,7 +260,7 @@ def pfasst_run(ctx: Context, u0, uT, allow_notconv=False):
 def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2, sweeps_coarse=1,
                 slices=1, iters=20, tol_sdc=1e-10, predictor=1, nu1=2, nu2=1, max_cycles=50,
                 mg_tol=1e-10, precision=FP64, forcing=FORCING_PAPER_LITERAL, batch=1, device=0,
-                use_graphs=0, autotune=1) -> Config:
+                use_graphs=0, autotune=1, inner=1) -> Config:
     """fine, coarse: (N, order, M) tuples; coarse None gives single-level SDC."""
     cfg = heat3d_config_default()
     cfg.nu, cfg.T, cfg.dt = nu, T, dt
@@ -269,7 +270,7 @@ def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2,
         cfg.levels[1] = Level(*coarse)
     cfg.sweeps_fine, cfg.sweeps_coarse = sweeps_fine, sweeps_coarse
     cfg.slices, cfg.iters, cfg.tol_sdc, cfg.predictor = slices, iters, tol_sdc, predictor
-    cfg.mg = MG(nu1, nu2, max_cycles, mg_tol)
+    cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner)
     cfg.precision, cfg.forcing, cfg.batch, cfg.device = precision, forcing, batch, device
     cfg.use_graphs = use_graphs
     cfg.autotune = autotune
@@ -309,3 +310,88 @@ def mg_vcycle_noalloc(N, order, precision, c, rhs, u, max_cycles, tol, stream=No
     if rc != OK and not (allow_notconv and rc == ENOTCONV):
         raise Heat3DError(rc, load().mg_vcycle_noalloc_last_error().decode())
     return rc, st.as_dict()
+
+
+class Server:
+    """Continuous-batching server (heat3d_server_*) over a torch-allocated pool."""
+
+    def __init__(self, pool, max_active=8, sweeps=4, precision=FP64, mg_tol=1e-10,
+                 max_cycles=50, nu1=2, nu2=1, inner=1, device=0):
+        self.pool = pool  # keep the memory alive
+        cfg = ServerConfig()
+        cfg.device = device
+        cfg.pool = C.c_void_p(pool.data_ptr())
+        cfg.pool_bytes = pool.numel() * pool.element_size()
+        cfg.max_active, cfg.sweeps, cfg.precision = max_active, sweeps, precision
+        cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner)
+        h = C.c_void_p()
+        rc = load().heat3d_server_create(C.byref(cfg), C.byref(h))
+        if rc != OK:
+            raise Heat3DError(rc, "server creation failed")
+        self.h = h
+        self._sizes = {}
+
+    def _err(self, rc):
+        raise Heat3DError(rc, load().heat3d_server_last_error(self.h).decode())
+
+    def submit(self, req) -> int:
+        """req: paper_1307_7867_gb300.inputs.Request (or anything with N, nu, T, dt, modes)."""
+        r = Request()
+        r.N, r.nu, r.T, r.dt = req.N, req.nu, req.T, req.dt
+        r.nmodes = len(req.modes)
+        for m, (k1, k2, k3, a) in enumerate(req.modes):
+            r.k[m][0], r.k[m][1], r.k[m][2] = k1, k2, k3
+            r.amp[m] = a
+        t = C.c_uint64()
+        rc = load().heat3d_submit(self.h, C.byref(r), C.byref(t))
+        if rc != OK:
+            self._err(rc)
+        self._sizes[t.value] = req.N
+        return t.value
+
+    def poll(self, ticket) -> bool:
+        d = C.c_int(0)
+        rc = load().heat3d_poll(self.h, C.c_uint64(ticket), C.byref(d))
+        if rc != OK:
+            self._err(rc)
+        return bool(d.value)
+
+    def wait(self, ticket, out=None):
+        """Blocks until done; returns (u(T) as a dense N^3 array, stats dict).  `out` may
+        be a preallocated numpy array or CUDA tensor of N^3 float64."""
+        st = Stats()
+        N = self._sizes.pop(ticket, None)
+        if out is None:
+            if N is None:
+                raise Heat3DError(EINVAL, "unknown ticket")
+            out = np.empty((N, N, N))
+        rc = load().heat3d_wait(self.h, C.c_uint64(ticket), _ptr(out), C.byref(st))
+        if rc not in (OK, ENOTCONV):
+            self._err(rc)
+        return out, st.as_dict()
+
+    def latency(self):
+        p50, p99 = C.c_double(), C.c_double()
+        n = C.c_longlong()
+        load().heat3d_server_latency(self.h, C.byref(p50), C.byref(p99), C.byref(n))
+        return p50.value, p99.value, n.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().heat3d_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def group_bytes_estimate(N, max_active=1, precision=FP64):
+    """Pool bytes one grid-size group of the server needs (workspace + state)."""
+    cfg = make_config((N, 2, 3), precision=precision, batch=max_active)
+    n = heat3d_workspace_size(cfg)
+    px = (N + 3) // 4 * 4
+    fs = (px * N * N + 63) // 64 * 64
+    return n + fs * 8 * max_active + 8 * (3 * N * 8 + 8) + 1024

@@ -70,7 +70,8 @@ def request_stream(n: int, rate: float, seed: int = 1307, sizes=(63, 127, 255),
     t = 0.0
     out = []
     for rid in range(n):
-        t += rng.exponential(1.0 / rate) if rate > 0 else 0.0
+        gap = rng.exponential(1.0)  # drawn at every rate, so the requests do not depend on it
+        t += gap / rate if rate > 0 else 0.0
         N = int(rng.choice(sizes))
         nu = float(rng.uniform(0.05, 0.2))
         T = float(rng.choice(horizons))
