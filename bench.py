@@ -334,6 +334,23 @@ def run_reference(args, w):
                     "d2h_bytes_per_step": 0}}
 
 
+def profile_step(w, precision):
+    """One time step of the workload with the iteration count capped at one (after
+    the coarse predictor): every kernel kind of the step, a few thousand launches."""
+    import torch
+    from paper_1307_7867_gb300 import build, heat3d as H, inputs
+    build.build()
+    w1 = dict(w, iters=1, tol_sdc=-1.0)
+    ctx = H.Context(make_cfg(H, w1, precision=precision), stream=torch.cuda.Stream())
+    u0 = torch.from_numpy(inputs.sine_mode(w["fine"][0])).cuda()
+    uT = torch.empty_like(u0)
+    n0 = H.heat3d_kernel_launches()
+    rc, st = H.pfasst_run(ctx, u0, uT, allow_notconv=True)
+    torch.cuda.synchronize()
+    return {"profile_step": precision, "launches": H.heat3d_kernel_launches() - n0,
+            "vcycles": st["vcycles"], "ms": st["seconds"] * 1e3}
+
+
 def kernel_case(w, precision):
     """Two fixed V(2,1) cycles of the workload's first fine substep solve: a small
     launch sequence (a few dozen kernels) for kernel-level profiling."""
@@ -428,6 +445,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
+    ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
+                    help="profiling case: one step of the workload capped at one iteration")
     ap.add_argument("--kernel-case", choices=["fp64", "mixed"], default=None,
                     help="profiling case: two fixed V(2,1) cycles of one fine-level solve only")
     args = ap.parse_args()
@@ -445,6 +464,9 @@ def main():
 
     if args.kernel_case:
         print(json.dumps(kernel_case(w, args.kernel_case)), flush=True)
+        return
+    if args.profile_step:
+        print(json.dumps(profile_step(w, args.profile_step)), flush=True)
         return
 
     if args.impl == "reference":

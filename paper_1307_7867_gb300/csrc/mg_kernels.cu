@@ -81,45 +81,93 @@ __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rr, T* __rest
   bc[p.b * gc.fs + p.idx] = s;
 }
 
-// Trilinear prolongation: fine (0-based) index i corresponds to the 1-based
-// fine index i+1; even 1-based indices sit on coarse points, odd ones average
-// the two coarse neighbours (zero outside).
+// Trilinear prolongation, one thread per coarse cell.  In 1-based indices the
+// cell C = 0..Nc spans coarse points C and C+1 (0 and Nc+1 are the Dirichlet
+// zeros) and owns the fine points 2C+1 (midway: mean of the two) and 2C+2 (on
+// coarse point C+1), per axis; in 0-based fine indices those are 2C and 2C+1,
+// so x-pairs are read and written as aligned two-element vectors.  The eight
+// corner values are combined axis by axis (x, then y, then z) and scaled by
+// 1/2 per averaged axis: 27 arithmetic operations per 8 fine points, no
+// divergent branches.
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> { using type = double2; };
+template <>
+struct Vec2<float> { using type = float2; };
+
+template <typename T>
+__device__ __forceinline__ T cval(const T* __restrict__ e, const Grid& gc, int i, int j, int k) {
+  if (i < 0 || i >= gc.N || j < 0 || j >= gc.N || k < 0 || k >= gc.N) return T(0);
+  return ldg(e + (long long)k * gc.plane + (long long)j * gc.px + i);
+}
+
 template <typename T>
 __global__ void k_prolong_add(Grid gc, Grid gf, const T* __restrict__ ec, long long ecs,
                               T* __restrict__ uf, long long ufs, const int* active) {
-  PointIdx p;
-  if (!point_index(gf, p)) return;
-  if (active && !active[p.b]) return;
-  const T* e = ec + p.b * ecs;
-  int ia[2], ja[2], ka[2], ni, nj, nk;
-  // 1-based fine index I = i + 1; coarse 1-based neighbours I/2 or (I-1)/2,(I+1)/2; to 0-based: -1
-  {
-    int I = p.i + 1;
-    if ((I & 1) == 0) { ia[0] = I / 2 - 1; ni = 1; } else { ia[0] = (I - 1) / 2 - 1; ia[1] = (I + 1) / 2 - 1; ni = 2; }
-    int J = p.j + 1;
-    if ((J & 1) == 0) { ja[0] = J / 2 - 1; nj = 1; } else { ja[0] = (J - 1) / 2 - 1; ja[1] = (J + 1) / 2 - 1; nj = 2; }
-    int K = p.k + 1;
-    if ((K & 1) == 0) { ka[0] = K / 2 - 1; nk = 1; } else { ka[0] = (K - 1) / 2 - 1; ka[1] = (K + 1) / 2 - 1; nk = 2; }
-  }
-  const int Nc = gc.N;
-  const T scale = T(1) / T(ni * nj * nk);
-  T s = T(0);
-  for (int c = 0; c < nk; ++c) {
-    int kk = ka[c];
-    if (kk < 0 || kk >= Nc) continue;
-    for (int b = 0; b < nj; ++b) {
-      int jj = ja[b];
-      if (jj < 0 || jj >= Nc) continue;
-      const T* row = e + (long long)kk * gc.plane + (long long)jj * gc.px;
-      for (int a = 0; a < ni; ++a) {
-        int ii = ia[a];
-        if (ii < 0 || ii >= Nc) continue;
-        s += ldg(row + ii) * scale;
+  using V2 = typename Vec2<T>::type;
+  const int nc1 = gc.N + 1;  // cells per axis
+  const int cx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int b = blockIdx.z / nc1;
+  const int cz = blockIdx.z - b * nc1;
+  if (cx >= nc1 || cy >= nc1) return;
+  if (active && !active[b]) return;
+  const T* e = ec + b * ecs;
+  // corner values v[z][y][x], 0 = low (coarse 0-based C-1), 1 = high (C)
+  T v[2][2][2];
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y)
+#pragma unroll
+      for (int x = 0; x < 2; ++x) v[z][y][x] = cval(e, gc, cx - 1 + x, cy - 1 + y, cz - 1 + z);
+  // x: A = sum of the pair (midpoint, scaled later), E = high value
+  T X[2][2][2];  // [z][y][mode x: 0 mid, 1 on-point]
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+      X[z][y][0] = v[z][y][0] + v[z][y][1];
+      X[z][y][1] = v[z][y][1];
+    }
+  T Y[2][2][2];  // [z][mode y][mode x]
+#pragma unroll
+  for (int z = 0; z < 2; ++z)
+#pragma unroll
+    for (int mx = 0; mx < 2; ++mx) {
+      Y[z][0][mx] = X[z][0][mx] + X[z][1][mx];
+      Y[z][1][mx] = X[z][1][mx];
+    }
+  const int Nf = gf.N;
+  const int fx = 2 * cx, fy0 = 2 * cy, fz0 = 2 * cz;  // 0-based fine index of the mid points
+  T* u = uf + b * ufs;
+#pragma unroll
+  for (int mz = 0; mz < 2; ++mz) {
+    const int fz = fz0 + mz;
+    if (fz >= Nf) continue;
+#pragma unroll
+    for (int my = 0; my < 2; ++my) {
+      const int fy = fy0 + my;
+      if (fy >= Nf) continue;
+      T val[2];
+#pragma unroll
+      for (int mx = 0; mx < 2; ++mx) {
+        T w = mz == 0 ? Y[0][my][mx] + Y[1][my][mx] : Y[1][my][mx];
+        const int na = (mx == 0) + (my == 0) + (mz == 0);  // averaged axes
+        val[mx] = na == 0 ? w : w * (na == 1 ? T(0.5) : na == 2 ? T(0.25) : T(0.125));
+      }
+      T* row = u + (long long)fz * gf.plane + (long long)fy * gf.px;
+      if (fx + 1 < Nf) {
+        V2 o = *reinterpret_cast<V2*>(row + fx);
+        o.x += val[0];
+        o.y += val[1];
+        *reinterpret_cast<V2*>(row + fx) = o;
+      } else if (fx < Nf) {
+        row[fx] += val[0];
       }
     }
   }
-  T* o = uf + p.b * ufs + p.idx;
-  *o = *o + s;
 }
 
 template <typename T>
@@ -196,8 +244,9 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
                                long long ec_stride, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  k_prolong_add<T><<<point_grid(gf, B), dim3(32, 8), 0, st>>>(gc, gf, ec, ec_stride, uf,
-                                                              uf_stride, active);
+  const int nc1 = gc.N + 1;
+  k_prolong_add<T><<<dim3((nc1 + 31) / 32, (nc1 + 7) / 8, nc1 * B), dim3(32, 8), 0, st>>>(
+      gc, gf, ec, ec_stride, uf, uf_stride, active);
   count_launch();
   return cudaGetLastError();
 }

@@ -998,13 +998,12 @@ static float time_shape(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1, Launch&& 
 
 static std::vector<Shape> shape_candidates(int N) {
   std::vector<Shape> v;
-  if (N < 8) {
-    v.push_back(Shape{1, N});
-    return v;
-  }
-  for (int kind = 1; kind <= 3; ++kind)
-    for (int zc : {4, 8, 16, 32, 64})
-      if (zc <= N) v.push_back(Shape{kind, zc});
+  for (int zc : {1, 2, 4, 8, 16, 32, 64})
+    if (zc <= N) v.push_back(Shape{1, zc});
+  if (N >= 16)
+    for (int kind = 2; kind <= 3; ++kind)
+      for (int zc : {2, 4, 8, 16, 32, 64})
+        if (zc <= N) v.push_back(Shape{kind, zc});
   return v;
 }
 
