@@ -54,7 +54,7 @@ extern "C" {
 /* One level of the space-time hierarchy (Sec. 1: PFASST coarsens nodes, mesh
  * and stencil order). */
 typedef struct {
-  int N;     /* interior points per axis; must be 2^k - 1 (multigrid halving) */
+  int N;     /* interior points per axis; must be 2^k - 1 (multigrid halving), <= 1023 */
   int order; /* 2: 7-point Laplacian; 4: 13-point wide Laplacian (odd-reflection ghosts) */
   int M;     /* Gauss-Lobatto nodes per step, both ends included, 2..5 */
 } heat3d_level;

@@ -11,6 +11,7 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -175,8 +176,8 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
   if (cfg->nlevels < 1 || cfg->nlevels > 2) return h3d_fail(c, HEAT3D_EINVAL, "nlevels must be 1 or 2");
   for (int l = 0; l < cfg->nlevels; ++l) {
     const heat3d_level& L = cfg->levels[l];
-    if (!is_pow2m1(L.N) || L.N > (1 << 11) - 1)
-      return h3d_fail(c, HEAT3D_EINVAL, "level %d: N=%d must be 2^k-1 (<= 2047)", l, L.N);
+    if (!is_pow2m1(L.N) || L.N > (1 << 10) - 1)
+      return h3d_fail(c, HEAT3D_EINVAL, "level %d: N=%d must be 2^k-1 (<= 1023)", l, L.N);
     if (L.order != 2 && L.order != 4) return h3d_fail(c, HEAT3D_EINVAL, "level %d: order must be 2 or 4", l);
     if (L.M < 2 || L.M > kMaxNodes) return h3d_fail(c, HEAT3D_EINVAL, "level %d: M must be 2..5", l);
   }
@@ -996,12 +997,17 @@ static float time_shape(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1, Launch&& 
   return best;
 }
 
+static bool tune_log() {
+  const char* v = getenv("HEAT3D_TUNE_LOG");
+  return v && v[0] == '1';
+}
+
 static std::vector<Shape> shape_candidates(int N) {
   std::vector<Shape> v;
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
     if (zc <= N) v.push_back(Shape{1, zc});
   if (N >= 16)
-    for (int kind = 2; kind <= 3; ++kind)
+    for (int kind = 2; kind <= 4; ++kind)
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
   return v;
@@ -1023,6 +1029,9 @@ static int autotune_T(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1) {
         float ms = time_shape(c, e0, e1, [&] {
           return launch_jacobi<T>(L.L.order, g, L.B, e, b, t, nullptr, 0, cf, nullptr, sh, c->st);
         });
+        if (tune_log())
+          fprintf(stderr, "tune jacobi T%zu order %d N %d B %d kind %d zc %d: %.4f ms\n", sizeof(T),
+                  L.L.order, g.N, L.B, sh.kind, sh.zc, ms);
         if (ms < best) { best = ms; pick = sh; }
       }
       L.shapeT[k] = pick;

@@ -97,6 +97,8 @@ __device__ __forceinline__ T combine(T s1, T s2) {
 // ---------------------------------------------------------------------------
 
 // F = alpha_b L u (and the next substep's rhs add_dst = u + add_src).
+// Operators take 32-bit offsets within the item (fields are < 2^31 elements);
+// init(b) resolves the item's base pointers once.
 template <int ORDER>
 struct OpLap {
   using T = double;
@@ -106,15 +108,21 @@ struct OpLap {
   const double* alpha;
   const double* add_src; double* add_dst; long long as;
   double a;
+  double* o_;
+  const double* as_;
+  double* ad_;
   __device__ const double* src(int b) const { return u + b * us; }
-  __device__ void init(int b) { a = alpha[b]; }
-  __device__ Ex load(int b, long long idx) const {
-    return Ex{add_src ? add_src[b * as + idx] : 0.0};
+  __device__ void init(int b) {
+    a = alpha[b];
+    o_ = out + b * os;
+    as_ = add_src ? add_src + b * as : nullptr;
+    ad_ = add_src ? add_dst + b * as : nullptr;
   }
-  __device__ double apply(int b, long long idx, double c, double s1, double s2, const Ex& ex) {
+  __device__ Ex load(int idx) const { return Ex{as_ ? as_[idx] : 0.0}; }
+  __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
     double L = ORDER == 2 ? fma(-6.0, c, s1) : fma(-90.0, c, fma(16.0, s1, -s2));
-    out[b * os + idx] = a * L;
-    if (add_src) add_dst[b * as + idx] = c + ex.add;
+    o_[idx] = a * L;
+    if (ad_) ad_[idx] = c + ex.add;
     return 0.0;
   }
 };
@@ -129,19 +137,25 @@ struct OpResid64 {
   const Coef<double>* coef;
   TR* r; TR* e0; const Coef<TR>* coef_r; long long rs;
   double d, e; TR wd;
+  const double* b_;
+  TR* r_;
+  TR* e0_;
   __device__ const double* src(int b) const { return u + b * us; }
   __device__ void init(int b) {
     d = coef[b].d;
     e = coef[b].e;
     wd = e0 ? coef_r[b].wd : TR(0);
+    b_ = bb + b * bs;
+    r_ = r + b * rs;
+    e0_ = e0 ? e0 + b * rs : nullptr;
   }
-  __device__ Ex load(int b, long long idx) const { return Ex{bb[b * bs + idx]}; }
-  __device__ double apply(int b, long long idx, double c, double s1, double s2, const Ex& ex) {
+  __device__ Ex load(int idx) const { return Ex{b_[idx]}; }
+  __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
     double S = combine<double, ORDER>(s1, s2);
     double res = fma(-d, c, fma(e, S, ex.b));
     TR rt = (TR)res;
-    r[b * rs + idx] = rt;
-    if (e0) e0[b * rs + idx] = wd * rt;
+    r_[idx] = rt;
+    if (e0_) e0_[idx] = wd * rt;
     return res;
   }
 };
@@ -155,17 +169,25 @@ struct OpJacobi {
   double* u64; long long u64s;
   const Coef<T>* coef;
   T d, ec, wd;
+  const T* r_;
+  T* o_;
+  double* u_;
   __device__ const T* src(int b) const { return e + b * fs; }
-  __device__ void init(int b) { d = coef[b].d; ec = coef[b].e; wd = coef[b].wd; }
-  __device__ Ex load(int b, long long idx) const {
-    return Ex{r[b * fs + idx], u64 ? u64[b * u64s + idx] : 0.0};
+  __device__ void init(int b) {
+    d = coef[b].d;
+    ec = coef[b].e;
+    wd = coef[b].wd;
+    r_ = r + b * fs;
+    o_ = out ? out + b * fs : nullptr;
+    u_ = u64 ? u64 + b * u64s : nullptr;
   }
-  __device__ double apply(int b, long long idx, T c, T s1, T s2, const Ex& ex) {
+  __device__ Ex load(int idx) const { return Ex{r_[idx], u_ ? u_[idx] : 0.0}; }
+  __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
     T S = combine<T, ORDER>(s1, s2);
     T res = fma(-d, c, fma(ec, S, ex.r));
     T v = fma(wd, res, c);
-    if (u64) u64[b * u64s + idx] = ex.u + (double)v;
-    else out[b * fs + idx] = v;
+    if (u_) u_[idx] = ex.u + (double)v;
+    else o_[idx] = v;
     return 0.0;
   }
 };
@@ -178,12 +200,19 @@ struct OpResid {
   const T* e; const T* r; T* rr; long long fs;
   const Coef<T>* coef;
   T d, ec;
+  const T* r_;
+  T* o_;
   __device__ const T* src(int b) const { return e + b * fs; }
-  __device__ void init(int b) { d = coef[b].d; ec = coef[b].e; }
-  __device__ Ex load(int b, long long idx) const { return Ex{r[b * fs + idx]}; }
-  __device__ double apply(int b, long long idx, T c, T s1, T s2, const Ex& ex) {
+  __device__ void init(int b) {
+    d = coef[b].d;
+    ec = coef[b].e;
+    r_ = r + b * fs;
+    o_ = rr + b * fs;
+  }
+  __device__ Ex load(int idx) const { return Ex{r_[idx]}; }
+  __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
     T S = combine<T, ORDER>(s1, s2);
-    rr[b * fs + idx] = fma(-d, c, fma(ec, S, ex.r));
+    o_[idx] = fma(-d, c, fma(ec, S, ex.r));
     return 0.0;
   }
 };
@@ -211,16 +240,17 @@ __global__ void __launch_bounds__(128) k_zmarch(Grid g, int nzc, int zc, const i
     T q[2 * R + 1];
 #pragma unroll
     for (int d = -R; d <= R; ++d) q[R + d] = at(u, g, i, j, z0 + d);
-    for (int k = z0; k < z1; ++k) {
-      const long long idx = (long long)k * g.plane + (long long)j * g.px + i;
-      typename Op::Ex ex = o.load(b, idx);
+    const int plane = (int)g.plane;
+    int idx = z0 * plane + j * g.px + i;
+    for (int k = z0; k < z1; ++k, idx += plane) {
+      typename Op::Ex ex = o.load(idx);
       T s1 = ((at(u, g, i - 1, j, k) + at(u, g, i + 1, j, k)) +
               (at(u, g, i, j - 1, k) + at(u, g, i, j + 1, k))) + (q[R - 1] + q[R + 1]);
       T s2 = T(0);
       if (R == 2)
         s2 = ((at(u, g, i - 2, j, k) + at(u, g, i + 2, j, k)) +
               (at(u, g, i, j - 2, k) + at(u, g, i, j + 2, k))) + (q[0] + q[2 * R]);
-      double rv = o.apply(b, idx, q[R], s1, s2, ex);
+      double rv = o.apply(idx, q[R], s1, s2, ex);
       if (NORM) {
         unsigned long long bits = abs_bits(rv);
         mx = bits > mx ? bits : mx;
@@ -242,6 +272,9 @@ constexpr int tile_smem_bytes() {
          (32 + 2 * halo_x<T>()) * (int)sizeof(T);
 }
 
+__device__ __forceinline__ int ring_next(int s, int nb) { return s + 1 == nb ? 0 : s + 1; }
+__device__ __forceinline__ int ring_prev(int s, int nb) { return s == 0 ? nb - 1 : s - 1; }
+
 template <int ORDER, int TYT, int RY, int D, bool NORM, typename Op>
 __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, const int* active,
                                                    unsigned long long* norm_bits, Op op) {
@@ -258,6 +291,7 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   const int b = blockIdx.z / nzc;
   if (active && !active[b]) return;  // uniform over the block
   const int N = g.N;
+  const int plane = (int)g.plane;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const int z0 = (blockIdx.z - b * nzc) * zc, z1 = min(N, z0 + zc);
   Op o = op;
@@ -265,59 +299,75 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   const T* __restrict__ u = o.src(b);
   const int tid = threadIdx.y * 32 + threadIdx.x;
 
-  // Plane z into its ring slot: interior 16-byte chunks by cp.async, the rest
-  // (domain halo, ghost planes) by plain loads under the boundary rule.
-  auto issue = [&](int z) {
+  // Plane z into ring slot `slot`: interior 16-byte chunks by cp.async, the
+  // rest (domain halo, ghost planes) by plain loads under the boundary rule.
+  // A thread's chunks are the same for every plane: offsets computed once.
+  constexpr int NCH = (SY * CH + NT - 1) / NT;
+  int soff[NCH], cgx[NCH], cgy[NCH], goff[NCH];
+  bool fast[NCH];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int c = tid + q * NT;
+    const int ry = c / CH, cx = c - ry * CH;
+    cgy[q] = y0 - R + ry;
+    cgx[q] = x0 - XH + cx * XH;
+    soff[q] = c < SY * CH ? ry * SX + cx * XH : -1;
+    goff[q] = cgy[q] * g.px + cgx[q];
+    fast[q] = cgy[q] >= 0 && cgy[q] < N && cgx[q] >= 0 && cgx[q] + XH <= N;
+  }
+  auto issue = [&](int z, int slot) {
     if (z <= z1 - 1 + R) {
-      T* dst = ring + ((z - z0 + R) % NB) * PS;
+      T* dst = ring + slot * PS;
       const bool zin = z >= 0 && z < N;
-      for (int c = tid; c < SY * CH; c += NT) {
-        const int ry = c / CH, cx = c - ry * CH;
-        const int gy = y0 - R + ry, gx = x0 - XH + cx * XH;
-        T* d = dst + ry * SX + cx * XH;
-        if (zin && gy >= 0 && gy < N && gx >= 0 && gx + XH <= N) {
-          cp_async16(d, u + (long long)z * g.plane + (long long)gy * g.px + gx);
+      const T* uz = u + z * plane;
+#pragma unroll
+      for (int q = 0; q < NCH; ++q) {
+        if (soff[q] < 0) continue;
+        T* d = dst + soff[q];
+        if (zin && fast[q]) {
+          cp_async16(d, uz + goff[q]);
         } else {
 #pragma unroll
-          for (int e = 0; e < XH; ++e) d[e] = at_any(u, g, gx + e, gy, z);
+          for (int e = 0; e < XH; ++e) d[e] = at_any(u, g, cgx[q] + e, cgy[q], z);
         }
       }
     }
     cp_async_commit();
   };
 
-  for (int z = z0 - R; z < z0 + R + D; ++z) issue(z);
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) issue(z0 - R + q, q);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = x0 + tx;
+  const int jb = y0 + ty * RY;
+  const int sbase = (R + ty * RY) * SX + XH + tx;
+  int idx0 = z0 * plane + jb * g.px + i;
+  int cs = R;  // ring slot of plane k
   unsigned long long mx = 0ull;
-  for (int k = z0; k < z1; ++k) {
+  for (int k = z0; k < z1; ++k, idx0 += plane) {
     typename Op::Ex ex[RY];
-    long long idx[RY];
 #pragma unroll
-    for (int r = 0; r < RY; ++r) {
-      const int j = y0 + ty * RY + r;
-      idx[r] = (long long)k * g.plane + (long long)j * g.px + i;
-      if (i < N && j < N) ex[r] = o.load(b, idx[r]);
-    }
+    for (int r = 0; r < RY; ++r)
+      if (i < N && jb + r < N) ex[r] = o.load(idx0 + r * g.px);
     cp_async_wait<D - 1>();
     __syncthreads();
-    const int base = k - z0 + R;
-    const T* P0 = ring + (base % NB) * PS;
-    const T* Pm1 = ring + ((base - 1) % NB) * PS;
-    const T* Pp1 = ring + ((base + 1) % NB) * PS;
-    const T* Pm2 = ring + ((base + NB - 2) % NB) * PS;
-    const T* Pp2 = ring + ((base + 2) % NB) * PS;
+    const int sm1 = ring_prev(cs, NB), sp1 = ring_next(cs, NB);
+    const int sm2 = ring_prev(sm1, NB), sp2 = ring_next(sp1, NB);
+    const T* P0 = ring + cs * PS + sbase;
+    const T* Pm1 = ring + sm1 * PS + sbase;
+    const T* Pp1 = ring + sp1 * PS + sbase;
+    const T* Pm2 = ring + sm2 * PS + sbase;
+    const T* Pp2 = ring + sp2 * PS + sbase;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
-      const int j = y0 + ty * RY + r;
-      const int o0 = (R + ty * RY + r) * SX + XH + tx;
+      const int o0 = r * SX;
       const T c = P0[o0];
       T s1 = ((P0[o0 - 1] + P0[o0 + 1]) + (P0[o0 - SX] + P0[o0 + SX])) + (Pm1[o0] + Pp1[o0]);
       T s2 = T(0);
       if (R == 2)
         s2 = ((P0[o0 - 2] + P0[o0 + 2]) + (P0[o0 - 2 * SX] + P0[o0 + 2 * SX])) + (Pm2[o0] + Pp2[o0]);
-      if (i < N && j < N) {
-        double rv = o.apply(b, idx[r], c, s1, s2, ex[r]);
+      if (i < N && jb + r < N) {
+        double rv = o.apply(idx0 + r * g.px, c, s1, s2, ex[r]);
         if (NORM) {
           unsigned long long bits = abs_bits(rv);
           mx = bits > mx ? bits : mx;
@@ -325,13 +375,15 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
       }
     }
     __syncthreads();
-    issue(k + R + D);
+    // the slot of plane k - R is free: fill it with plane k + R + D
+    issue(k + R + D, R == 2 ? sm2 : sm1);
+    cs = sp1;
   }
   cp_async_wait<0>();
   if (NORM) warp_max_to(mx, norm_bits + b);
 }
 
-constexpr int kTileD = 2;
+constexpr int kTileD = 3;
 
 template <int ORDER, bool NORM, typename Op>
 cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long long* norm_bits,
@@ -349,6 +401,12 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
     k_zmarch<ORDER, NORM, Op><<<grd, blk, 0, st>>>(g, nzc, zc, active, norm_bits, op);
   } else if (kind == 2) {
     constexpr int TYT = 4, RY = 2;
+    dim3 blk(32, TYT, 1);
+    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
+    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
+        g, nzc, zc, active, norm_bits, op);
+  } else if (kind == 4) {
+    constexpr int TYT = 4, RY = 4;
     dim3 blk(32, TYT, 1);
     dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
     k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
