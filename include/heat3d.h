@@ -90,6 +90,8 @@ typedef struct {
                                non-default stream; ignored on the legacy stream) */
   int autotune;             /* 1: time the stencil launch shapes of every multigrid level at
                                heat3d_bind_workspace and keep the fastest (results identical) */
+  int fuse_coarse;          /* 1: run the multigrid levels with N <= 15 of a V-cycle in one
+                               kernel, all levels in shared memory (results identical) */
 } heat3d_config;
 
 typedef struct {

@@ -69,6 +69,16 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
                                long long ec_stride, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st);
 
+// The whole V-cycle below (and including) a level with N <= 15, one block per
+// item, every level in shared memory (coarse_fused.cu).  Ns: sizes from that
+// level down to 1; cf[l]: coefficients of level l for item 0 of the launch;
+// b, e: the top level's right-hand side and correction (pitched, grid gtop).
+constexpr int kFusedMaxN = 15;
+template <typename T>
+cudaError_t launch_vcycle_small(int order, int nlev, const int* Ns, const Coef<T>* const* cf,
+                                int B, const T* b, T* e, const Grid& gtop, int nu1, int nu2,
+                                const int* active, cudaStream_t st);
+
 // u64 += e
 template <typename T>
 cudaError_t launch_update(const Grid& g, int B, const T* e, double* u64, long long u64_stride,

@@ -452,6 +452,20 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   T* t = mgbuf<T>(L, k, 2, b0);
   const Coef<T>* cf = coefT<T>(L, slot, k, b0);
   const size_t ts = sizeof(T), pts = (size_t)g.N * g.N * g.N * B;
+  if (k > 0 && c->cfg.fuse_coarse && g.N <= kFusedMaxN) {
+    // this level and every coarser one in a single kernel (same arithmetic)
+    int Ns[kMaxLevels];
+    const Coef<T>* cfs[kMaxLevels];
+    const int nl = L.nmg - k;
+    for (int l = 0; l < nl; ++l) {
+      Ns[l] = L.mg[k + l].N;
+      cfs[l] = coefT<T>(L, slot, k + l, b0);
+    }
+    CK(launch_vcycle_small<T>(order, nl, Ns, cfs, B, b, e, g, nu1, nu2, act, st));
+    c->bytes += 2.0 * ts * pts;
+    *result = e;
+    return HEAT3D_OK;
+  }
   if (g.N == 1) {
     CK(launch_jacobi_zero<T>(g, B, b, e, cf, true, act, st));
     if (k == 0 && final) {
@@ -1134,6 +1148,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->stream = nullptr;
   cfg->use_graphs = 0;
   cfg->autotune = 1;
+  cfg->fuse_coarse = 1;
 }
 
 int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes) {

@@ -231,15 +231,16 @@ def test_run_mixed_precision_matches_fp64_oracle(H, oracle):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graphs_and_autotune_change_nothing(H, oracle, precision):
-    """V-cycles replayed from CUDA graphs (private stream) and autotuned launch
-    shapes give bitwise the same MLSDC result as plain launches with the
-    default shapes; the FP64 run also matches the oracle."""
+    """V-cycles replayed from CUDA graphs (private stream), autotuned launch
+    shapes and the fused coarse-level kernel give bitwise the same MLSDC
+    result as plain launches with the default shapes; the FP64 run also
+    matches the oracle."""
     fine, coarse = (31, 4, 5), (15, 2, 3)
     prec = H.FP64 if precision == "fp64" else H.MIXED
     outs = []
-    for graphs, tune in ((0, 0), (1, 1), (1, 0)):
+    for graphs, tune, fuse in ((0, 0, 0), (1, 1, 1), (1, 0, 0), (0, 1, 1)):
         cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, precision=prec, mg_tol=1e-11,
-                            use_graphs=graphs, autotune=tune)
+                            use_graphs=graphs, autotune=tune, fuse_coarse=fuse)
         ctx = H.Context(cfg, stream=torch.cuda.Stream())
         u0 = inputs.sine_mode(31)
         uT = np.empty_like(u0)
