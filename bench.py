@@ -55,6 +55,12 @@ WORKLOADS = {
              "dt=1/16, 5 iterations, 1 fine sweep per iteration",
         fine=(127, 4, 5), coarse=(63, 2, 3), dt=1 / 16, sweeps_fine=1, sweeps_coarse=1,
         slices=16, iters=5, tol_sdc=-1.0, mg_tol=1e-11, precision="fp64", steps=16, warmup=16),
+    "paper": dict(
+        desc="the paper's setup with the wide fine stencil: PFASST on 32 slices of dt=0.1875 "
+             "(T=6), fine 255^3 wide M=5 / coarse 127^3 7-point M=3, 1 fine sweep per "
+             "iteration, iterated to residual 1e-10 (<= 50 iterations)",
+        fine=(255, 4, 5), coarse=(127, 2, 3), dt=0.1875, sweeps_fine=1, sweeps_coarse=1,
+        slices=32, iters=50, tol_sdc=1e-10, mg_tol=1e-11, precision="fp64", steps=32, warmup=0),
     "c4": dict(
         desc="mixed precision, fine 511^3 wide M=5 / coarse 255^3 7-point M=3, dt=1/32, "
              "MLSDC to residual 1e-10, FP32 V-cycles in FP64 refinement to 1e-11",
@@ -175,8 +181,9 @@ def run_ours(args, w, rank, world):
 
     ctx = H.Context(make_cfg(H, w, graphs=not args.no_graphs), stream=torch.cuda.Stream(dev))
     # warm-up steps (untimed)
-    H.heat3d_set_interval(ctx, 0.0, W * dt)
-    H.pfasst_run(ctx, u0_d, uT_d, allow_notconv=True)
+    if W > 0:
+        H.heat3d_set_interval(ctx, 0.0, W * dt)
+        H.pfasst_run(ctx, u0_d, uT_d, allow_notconv=True)
     # timed steps: K steps from t = 0 on device-resident buffers
     prof_class = H.PROF_JACOBI_FINE if w["precision"] == "fp64" else H.PROF_RESID64_FINE
     H.heat3d_profile(ctx, prof_class)
@@ -217,12 +224,14 @@ def run_ours(args, w, rank, world):
     uo = torch.empty_like(uh).pin_memory()
     barrier()
     t0 = time.perf_counter()
-    for s in range(0, K, P):
+    for s in range(0, K if not args.no_e2e else 0, P):
         H.heat3d_set_interval(ctx, s * dt, P * dt)
         H.pfasst_run(ctx, uh, uo, allow_notconv=True)
         uh, uo = uo, uh
     barrier()
-    e2e_secs = time.perf_counter() - t0
+    e2e_secs = max(time.perf_counter() - t0, 1e-9)
+    if args.no_e2e:
+        uh = torch.from_numpy(uT.copy())
     if world > 1:
         t = torch.tensor([e2e_secs], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -269,9 +278,10 @@ def run_ours(args, w, rank, world):
         "accuracy": {"rel_err_vs_pde_solution": err_pde, "rel_err_vs_semidiscrete": err_sd,
                      "t_end": tK},
         "roofline": roof,
-        "e2e": {"value": world * pts * K / e2e_secs, "unit": "grid-pt-steps/s",
-                "h2d_bytes_per_step": nbytes * 1.0 / P, "d2h_bytes_per_step": nbytes * 1.0 / P,
-                "max_abs_diff_vs_device_run": e2e_diff},
+        "e2e": None if args.no_e2e else {
+            "value": world * pts * K / e2e_secs, "unit": "grid-pt-steps/s",
+            "h2d_bytes_per_step": nbytes * 1.0 / P, "d2h_bytes_per_step": nbytes * 1.0 / P,
+            "max_abs_diff_vs_device_run": e2e_diff},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
@@ -433,18 +443,85 @@ def run_serving(args):
             "results_independent_of_batch": same}
 
 
+def run_alpha(args):
+    """The speedup model of Sec. 1.1 (Eq. pfasst_speedup) measured on one GB300 at
+    the 16-slice PFASST sizes (fine 127^3 wide M=5, coarse 63^3 7-point M=3,
+    dt = 1/16): alpha = coarse/fine sweep time, beta = FAS transfer time per
+    fine sweep, K_S = serial SDC sweeps per step and K_P = PFASST iterations to
+    the 1e-10 residual, and the model speedup s(P) beside the measured one
+    (serial SDC over P steps / PFASST over P slices, both on this GPU)."""
+    import torch
+    from paper_1307_7867_gb300 import build, heat3d as H, inputs
+    build.build()
+    fine, coarse, dt = (127, 4, 5), (63, 2, 3), 1 / 16
+    u0 = inputs.sine_mode(127)
+    st_ = torch.cuda.Stream()
+
+    def ctx_for(P, nlevels=2, sweeps=1):
+        cfg = H.make_config(fine, coarse if nlevels == 2 else None, dt=dt, T=P * dt,
+                            sweeps_fine=sweeps, sweeps_coarse=1, slices=P if nlevels == 2 else 1,
+                            iters=50, tol_sdc=1e-10, mg_tol=1e-11, batch=max(P, 1),
+                            use_graphs=1, autotune=1)
+        return H.Context(cfg, stream=st_)
+
+    # alpha and beta from single-slice sweeps on a representative state
+    c = ctx_for(1)
+    H.heat3d_set_state(c, 0, 0, 0.0, u0)
+    H.heat3d_set_state(c, 1, 0, 0.0, np.ascontiguousarray(u0[1::2, 1::2, 1::2]))
+    for _ in range(2):
+        H.sdc_sweep(c, 0, 0, 1)
+    tf, tc, tr = [], [], []
+    for _ in range(5):
+        t0 = time.perf_counter(); H.sdc_sweep(c, 0, 0, 1); tf.append(time.perf_counter() - t0)
+        t0 = time.perf_counter(); H.heat3d_fas_restrict(c, 0, 1); H.heat3d_fas_interpolate(c, 0, 1)
+        tr.append(time.perf_counter() - t0)
+        H.heat3d_fas_restrict(c, 0, 1)
+        t0 = time.perf_counter(); H.sdc_sweep(c, 1, 0, 1); tc.append(time.perf_counter() - t0)
+    t_f, t_c, t_r = statistics.median(tf), statistics.median(tc), statistics.median(tr)
+    alpha, beta = t_c / t_f, t_r / t_f
+    # K_S: serial single-level SDC, sweeps to the residual threshold
+    Pmax = 16
+    cs = H.Context(H.make_config(fine, None, dt=dt, T=Pmax * dt, sweeps_fine=50, tol_sdc=1e-10,
+                                 mg_tol=1e-11, use_graphs=1, autotune=1), stream=st_)
+    uT = np.empty_like(u0)
+    H.pfasst_run(cs, u0, uT)  # warm-up
+    t0 = time.perf_counter(); rc, ss = H.pfasst_run(cs, u0, uT); t_serial16 = time.perf_counter() - t0
+    K_S = ss["sweeps"] / Pmax
+    rows = []
+    for P in (1, 2, 4, 8, 16):
+        cp = ctx_for(P)
+        H.pfasst_run(cp, u0, uT, allow_notconv=True)
+        t0 = time.perf_counter()
+        rc, sp = H.pfasst_run(cp, u0, uT, allow_notconv=True)
+        t_p = time.perf_counter() - t0
+        K_P = sp["iters"]
+        model = K_S * P / (P * alpha + K_P * (1 + alpha + beta))
+        measured = (t_serial16 * P / Pmax) / t_p
+        rows.append({"P": P, "K_P": K_P, "seconds": t_p, "speedup_model": model,
+                     "speedup_measured": measured, "residual": sp["residual"]})
+        cp.close()
+    return {"workload": "speedup model (Eq. pfasst_speedup) on one GB300: fine 127^3 wide M=5, "
+                        "coarse 63^3 7-point M=3, dt=1/16, residual 1e-10",
+            "alpha": alpha, "beta": beta, "K_S": K_S, "t_fine_sweep_s": t_f,
+            "t_coarse_sweep_s": t_c, "t_fas_s": t_r, "t_serial_sdc_16_steps_s": t_serial16,
+            "pfasst": rows,
+            "paper_alpha": {"bgq_small": 0.083, "bgq_large": 0.36, "xe6_small": 0.086,
+                            "xe6_large": 0.4}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=None)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5"])
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS) + ["c5", "alpha"])
     ap.add_argument("--requests", type=int, default=32, help="c5: requests in the stream")
     ap.add_argument("--pool-gb", type=float, default=40.0, help="c5: server pool size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
                     help="profiling case: one step of the workload capped at one iteration")
     ap.add_argument("--kernel-case", choices=["fp64", "mixed"], default=None,
@@ -453,6 +530,10 @@ def main():
     if args.workload == "c5":
         if int(os.environ.get("RANK", 0)) == 0:
             print(json.dumps(run_serving(args)), flush=True)
+        return
+    if args.workload == "alpha":
+        if int(os.environ.get("RANK", 0)) == 0:
+            print(json.dumps(run_alpha(args)), flush=True)
         return
     w = WORKLOADS[args.workload]
     args.steps = args.steps or w["steps"]
@@ -487,8 +568,9 @@ def main():
                        stream=torch.cuda.Stream())
         u0_d = torch.from_numpy(u0).cuda()
         o = torch.empty_like(u0_d)
-        H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
-        H.pfasst_run(cm, u0_d, o, allow_notconv=True)
+        if args.warmup > 0:
+            H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
+            H.pfasst_run(cm, u0_d, o, allow_notconv=True)
         H.heat3d_set_interval(cm, 0.0, args.steps * w["dt"])
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
