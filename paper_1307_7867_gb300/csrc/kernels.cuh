@@ -12,7 +12,8 @@ namespace h3d {
 // kind: 0 automatic (tiled for N >= 32, else z-march), 1 z-march (one column
 // per thread), 2 shared-memory tile 32 x 8 (128 threads, 2 rows each), 3 tile
 // 32 x 16 (256 threads, 2 rows each), 4 tile 32 x 16 (128 threads, 4 rows
-// each); zc: planes per block along z.
+// each), 5 and 6 as 2 and 3 with 6 planes of prefetch instead of 3; zc:
+// planes per block along z.
 struct Shape {
   int kind = 0;
   int zc = 16;

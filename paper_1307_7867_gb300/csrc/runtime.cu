@@ -1021,7 +1021,7 @@ static std::vector<Shape> shape_candidates(int N) {
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
     if (zc <= N) v.push_back(Shape{1, zc});
   if (N >= 16)
-    for (int kind = 2; kind <= 4; ++kind)
+    for (int kind = 2; kind <= 6; ++kind)
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
   return v;

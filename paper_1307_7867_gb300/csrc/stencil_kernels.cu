@@ -96,10 +96,11 @@ __device__ __forceinline__ T combine(T s1, T s2) {
 // operators
 // ---------------------------------------------------------------------------
 
-// F = alpha_b L u (and the next substep's rhs add_dst = u + add_src).
+// F = alpha_b L u (and, when ADD, the next substep's rhs add_dst = u + add_src).
 // Operators take 32-bit offsets within the item (fields are < 2^31 elements);
-// init(b) resolves the item's base pointers once.
-template <int ORDER>
+// init(b) resolves the item's base pointers once.  Optional outputs are
+// template parameters so that unused FP64 work is not executed.
+template <int ORDER, bool ADD>
 struct OpLap {
   using T = double;
   struct Ex { double add; };
@@ -115,14 +116,20 @@ struct OpLap {
   __device__ void init(int b) {
     a = alpha[b];
     o_ = out + b * os;
-    as_ = add_src ? add_src + b * as : nullptr;
-    ad_ = add_src ? add_dst + b * as : nullptr;
+    if (ADD) {
+      as_ = add_src + b * as;
+      ad_ = add_dst + b * as;
+    }
   }
-  __device__ Ex load(int idx) const { return Ex{as_ ? as_[idx] : 0.0}; }
+  __device__ Ex load(int idx) const {
+    Ex x;
+    if (ADD) x.add = as_[idx];
+    return x;
+  }
   __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
     double L = ORDER == 2 ? fma(-6.0, c, s1) : fma(-90.0, c, fma(16.0, s1, -s2));
     o_[idx] = a * L;
-    if (ad_) ad_[idx] = c + ex.add;
+    if (ADD) ad_[idx] = c + ex.add;
     return 0.0;
   }
 };
@@ -160,8 +167,11 @@ struct OpResid64 {
   }
 };
 
-// Damped Jacobi on the error equation: v = e + wd (r - A e); stored, or added to u64.
-template <typename TT, int ORDER>
+// Damped Jacobi on the error equation: v = e + wd (r - A e); stored (UPD =
+// false) or added to the FP64 solution u64 (UPD = true).  UPD is a template
+// parameter so that the stored variant contains no FP64 instruction at all
+// (a runtime branch is if-converted and would run the FP64 add everywhere).
+template <typename TT, int ORDER, bool UPD>
 struct OpJacobi {
   using T = TT;
   struct Ex { T r; double u; };
@@ -178,15 +188,20 @@ struct OpJacobi {
     ec = coef[b].e;
     wd = coef[b].wd;
     r_ = r + b * fs;
-    o_ = out ? out + b * fs : nullptr;
-    u_ = u64 ? u64 + b * u64s : nullptr;
+    if (UPD) u_ = u64 + b * u64s;
+    else o_ = out + b * fs;
   }
-  __device__ Ex load(int idx) const { return Ex{r_[idx], u_ ? u_[idx] : 0.0}; }
+  __device__ Ex load(int idx) const {
+    Ex x;
+    x.r = r_[idx];
+    if (UPD) x.u = u_[idx];
+    return x;
+  }
   __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
     T S = combine<T, ORDER>(s1, s2);
     T res = fma(-d, c, fma(ec, S, ex.r));
     T v = fma(wd, res, c);
-    if (u_) u_[idx] = ex.u + (double)v;
+    if (UPD) u_[idx] = ex.u + (double)v;
     else o_[idx] = v;
     return 0.0;
   }
@@ -266,9 +281,11 @@ __global__ void __launch_bounds__(128) k_zmarch(Grid g, int nzc, int zc, const i
 template <typename T>
 __host__ __device__ constexpr int halo_x() { return 16 / (int)sizeof(T); }
 
+// Ring of 2R + D + 1 planes: the D planes in flight, the 2R + 1 planes being
+// read, and the slot refilled during the current plane.
 template <typename T, int ORDER, int TYT, int RY, int D>
 constexpr int tile_smem_bytes() {
-  return (2 * (ORDER == 2 ? 1 : 2) + D) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) *
+  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) *
          (32 + 2 * halo_x<T>()) * (int)sizeof(T);
 }
 
@@ -282,7 +299,7 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   constexpr int R = ORDER == 2 ? 1 : 2;
   constexpr int TX = 32, TY = TYT * RY;
   constexpr int XH = halo_x<T>();
-  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D;
+  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D + 1;
   constexpr int CH = SX / XH;  // 16-byte chunks per shared row
   constexpr int NT = 32 * TYT;
   constexpr int PS = SY * SX;  // elements per shared plane
@@ -336,13 +353,14 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   };
 
 #pragma unroll 1
-  for (int q = 0; q < NB; ++q) issue(z0 - R + q, q);
+  for (int q = 0; q < 2 * R + D; ++q) issue(z0 - R + q, q);
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int i = x0 + tx;
   const int jb = y0 + ty * RY;
   const int sbase = (R + ty * RY) * SX + XH + tx;
   int idx0 = z0 * plane + jb * g.px + i;
-  int cs = R;  // ring slot of plane k
+  int cs = R;                // ring slot of plane k
+  int fs_ = 2 * R + D;       // slot that receives plane k + R + D
   unsigned long long mx = 0ull;
   for (int k = z0; k < z1; ++k, idx0 += plane) {
     typename Op::Ex ex[RY];
@@ -350,7 +368,11 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
     for (int r = 0; r < RY; ++r)
       if (i < N && jb + r < N) ex[r] = o.load(idx0 + r * g.px);
     cp_async_wait<D - 1>();
+    // one barrier per plane: after it every thread has finished plane k - 1,
+    // so the slot of plane k - R - 1 can be refilled while plane k is computed
     __syncthreads();
+    issue(k + R + D, fs_);
+    fs_ = ring_next(fs_, NB);
     const int sm1 = ring_prev(cs, NB), sp1 = ring_next(cs, NB);
     const int sm2 = ring_prev(sm1, NB), sp2 = ring_next(sp1, NB);
     const T* P0 = ring + cs * PS + sbase;
@@ -374,50 +396,58 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
         }
       }
     }
-    __syncthreads();
-    // the slot of plane k - R is free: fill it with plane k + R + D
-    issue(k + R + D, R == 2 ? sm2 : sm1);
     cs = sp1;
   }
   cp_async_wait<0>();
   if (NORM) warp_max_to(mx, norm_bits + b);
 }
 
-constexpr int kTileD = 3;
+// One tiled launch: TYT warps per block, RY rows per thread, D planes of
+// prefetch.  Rings above 48 KB need the shared-memory opt-in (set once).
+template <int ORDER, int TYT, int RY, int D, bool NORM, typename Op>
+cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active,
+                        unsigned long long* norm_bits, const Op& op, cudaStream_t st) {
+  using T = typename Op::T;
+  constexpr int smem = tile_smem_bytes<T, ORDER, TYT, RY, D>();
+  if (smem > 48 * 1024) {
+    static bool set = false;
+    if (!set) {
+      cudaError_t e = cudaFuncSetAttribute(k_tile<ORDER, TYT, RY, D, NORM, Op>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      set = true;
+    }
+  }
+  dim3 blk(32, TYT, 1);
+  dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
+  k_tile<ORDER, TYT, RY, D, NORM, Op><<<grd, blk, smem, st>>>(g, nzc, zc, active, norm_bits, op);
+  return cudaSuccess;
+}
 
 template <int ORDER, bool NORM, typename Op>
 cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long long* norm_bits,
                         const Op& op, Shape sh, cudaStream_t st) {
-  using T = typename Op::T;
   if (B <= 0 || g.N <= 0) return cudaSuccess;
   int kind = sh.kind;
   if (kind == 0) kind = g.N >= 32 ? 3 : 1;
   int zc = sh.zc > 0 ? sh.zc : 16;
   if (zc > g.N) zc = g.N;
   const int nzc = (g.N + zc - 1) / zc;
-  if (kind == 1) {
-    dim3 blk(32, 4, 1);
-    dim3 grd((g.N + 31) / 32, (g.N + 3) / 4, nzc * B);
-    k_zmarch<ORDER, NORM, Op><<<grd, blk, 0, st>>>(g, nzc, zc, active, norm_bits, op);
-  } else if (kind == 2) {
-    constexpr int TYT = 4, RY = 2;
-    dim3 blk(32, TYT, 1);
-    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
-    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
-        g, nzc, zc, active, norm_bits, op);
-  } else if (kind == 4) {
-    constexpr int TYT = 4, RY = 4;
-    dim3 blk(32, TYT, 1);
-    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
-    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
-        g, nzc, zc, active, norm_bits, op);
-  } else {
-    constexpr int TYT = 8, RY = 2;
-    dim3 blk(32, TYT, 1);
-    dim3 grd((g.N + 31) / 32, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
-    k_tile<ORDER, TYT, RY, kTileD, NORM, Op><<<grd, blk, tile_smem_bytes<T, ORDER, TYT, RY, kTileD>(), st>>>(
-        g, nzc, zc, active, norm_bits, op);
+  cudaError_t e = cudaSuccess;
+  switch (kind) {
+    case 1: {
+      dim3 blk(32, 4, 1);
+      dim3 grd((g.N + 31) / 32, (g.N + 3) / 4, nzc * B);
+      k_zmarch<ORDER, NORM, Op><<<grd, blk, 0, st>>>(g, nzc, zc, active, norm_bits, op);
+      break;
+    }
+    case 2: e = launch_tile<ORDER, 4, 2, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
+    case 4: e = launch_tile<ORDER, 4, 4, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
+    case 5: e = launch_tile<ORDER, 4, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
+    case 6: e = launch_tile<ORDER, 8, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
+    default: e = launch_tile<ORDER, 8, 2, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
   }
+  if (e != cudaSuccess) return e;
   count_launch();
   return cudaGetLastError();
 }
@@ -432,11 +462,19 @@ cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long lo
                        double* out, long long out_stride, const double* alpha,
                        const double* add_src, double* add_dst, long long add_stride,
                        const int* active, Shape sh, cudaStream_t st) {
+  if (add_src) {
+    if (order == 2) {
+      OpLap<2, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+      return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+    }
+    OpLap<4, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+    return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (order == 2) {
-    OpLap<2> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+    OpLap<2, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
     return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
   }
-  OpLap<4> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+  OpLap<4, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
   return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
 }
 
@@ -460,11 +498,19 @@ template <typename T>
 cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
                           double* u64, long long u64_stride, const Coef<T>* coef,
                           const int* active, Shape sh, cudaStream_t st) {
+  if (u64) {
+    if (order == 2) {
+      OpJacobi<T, 2, true> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+      return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
+    }
+    OpJacobi<T, 4, true> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+    return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (order == 2) {
-    OpJacobi<T, 2> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+    OpJacobi<T, 2, false> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
     return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
   }
-  OpJacobi<T, 4> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+  OpJacobi<T, 4, false> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
   return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
 }
 
