@@ -147,6 +147,22 @@ def make_cfg(H, w, precision=None, slices=None, graphs=True):
                          use_graphs=1 if graphs else 0, autotune=1, inner=inner)
 
 
+def max_over_ranks(seconds, device, world):
+    """Slowest rank's time (MAX all-reduce); the value of a single rank alone."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(seconds)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(work_per_rank, seconds, world):
+    """Whole-job throughput of `world` independent replicas."""
+    return world * work_per_rank / seconds
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -200,13 +216,9 @@ def run_ours(args, w, rank, world):
     ms = ev0.elapsed_time(ev1)
     prof = H.heat3d_profile_read(ctx)
     H.heat3d_profile(ctx, H.PROF_OFF)
-    secs = ms / 1e3
-    if world > 1:
-        t = torch.tensor([secs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = max_over_ranks(ms / 1e3, dev, world)
     pts = float(Nf) ** 3
-    value = world * pts * K / secs
+    value = replica_value(pts * K, secs, world)
     uT = uT_d.cpu().numpy()
 
     # accuracy against the exact PDE solution and the semi-discrete solution
@@ -229,13 +241,9 @@ def run_ours(args, w, rank, world):
         H.pfasst_run(ctx, uh, uo, allow_notconv=True)
         uh, uo = uo, uh
     barrier()
-    e2e_secs = max(time.perf_counter() - t0, 1e-9)
+    e2e_secs = max_over_ranks(max(time.perf_counter() - t0, 1e-9), dev, world)
     if args.no_e2e:
         uh = torch.from_numpy(uT.copy())
-    if world > 1:
-        t = torch.tensor([e2e_secs], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_secs = float(t.item())
     e2e_diff = float(np.abs(uh.numpy() - uT).max())
     nbytes = Nf ** 3 * 8
 
