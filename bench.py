@@ -136,15 +136,17 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
-def make_cfg(H, w, precision=None, slices=None, graphs=True):
+def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None):
     prec = H.MIXED if (precision or w["precision"]) == "mixed" else H.FP64
+    # mg_rel > 0: each solve stops at max(mg_tol, mg_rel x the sweep's incoming residual)
+    mg_rel = w.get("mg_rel", 0.0) if mg_rel is None else mg_rel
     inner = 2 if prec == H.MIXED else 1  # FP32 V-cycles per FP64 residual
     return H.make_config(w["fine"], w["coarse"], dt=w["dt"], T=w["dt"],
                          sweeps_fine=w["sweeps_fine"], sweeps_coarse=w["sweeps_coarse"],
                          slices=slices or w["slices"], iters=w["iters"], tol_sdc=w["tol_sdc"],
                          mg_tol=w["mg_tol"], max_cycles=50, precision=prec,
                          forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"],
-                         use_graphs=1 if graphs else 0, autotune=1, inner=inner)
+                         use_graphs=1 if graphs else 0, autotune=1, inner=inner, mg_rel=mg_rel)
 
 
 def max_over_ranks(seconds, device, world):
@@ -278,7 +280,7 @@ def run_ours(args, w, rank, world):
         "ms_per_step": secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "f64+f32",
         "data": "synthetic (analytic initial value and forcing, Eqs. 3-4)",
-        "config": {"workload": w["desc"], "N_fine": Nf, "dt": dt,
+        "config": {"workload": w["desc"], "N_fine": Nf, "dt": dt, "mg_rel": w.get("mg_rel", 0.0),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "working set >> L2 (fields of 133 MB+), no flush needed"},
         "stats": {k: st[k] for k in ("vcycles", "vcycles_level", "solves", "sweeps", "iters",
@@ -294,6 +296,46 @@ def run_ours(args, w, rank, world):
         "clocks": clk.summary(),
     }
     return out, ctx, st, u0, uT
+
+
+# mg_rel of the adaptive-tolerance variants, per precision: the largest value of
+# {0.005, 0.01, 0.02, 0.05, 0.1} whose error against the PDE solution stays at
+# or below the fixed-tolerance FP64 run's on the 255^3 MLSDC workload
+ADAPTIVE_REL = {"fp64": 0.01, "mixed": 0.02}
+
+
+def run_variant(args, w, u0, uT, out, precision, mg_rel):
+    """The timed steps of the headline run again with another precision or
+    solver-tolerance rule; accuracy against the PDE solution and the FP64 run."""
+    import torch
+    from paper_1307_7867_gb300 import heat3d as H, inputs
+    cm = H.Context(make_cfg(H, w, precision=precision, graphs=not args.no_graphs, mg_rel=mg_rel),
+                   stream=torch.cuda.Stream())
+    u0_d = torch.from_numpy(u0).cuda()
+    o = torch.empty_like(u0_d)
+    if args.warmup > 0:
+        H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
+        H.pfasst_run(cm, u0_d, o, allow_notconv=True)
+    H.heat3d_set_interval(cm, 0.0, args.steps * w["dt"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(cm.stream)
+    rc, sm = H.pfasst_run(cm, u0_d, o, allow_notconv=True)
+    e1.record(cm.stream)
+    torch.cuda.synchronize()
+    s_m = e0.elapsed_time(e1) / 1e3
+    um = o.cpu().numpy()
+    Nf = w["fine"][0]
+    a_pde = analytic_amplitude(args.steps * w["dt"])
+    err_m = float(np.abs(um - a_pde * inputs.sine_mode(Nf)).max() / abs(a_pde))
+    cm.close()
+    return {"precision": precision, "mg_rel": mg_rel,
+            "value": Nf ** 3 * args.steps / s_m, "ms_per_step": s_m * 1e3 / args.steps,
+            "rel_err_vs_pde_solution": err_m,
+            "max_rel_diff_vs_fp64": float(np.abs(um - uT).max() / np.abs(uT).max()),
+            "vcycles": sm["vcycles"], "vcycles_level": list(sm["vcycles_level"]),
+            "iters": sm["iters"], "residual": sm["residual"],
+            "equal_error": err_m <= 1.01 * out["accuracy"]["rel_err_vs_pde_solution"]}
 
 
 def oracle_sample_fine_vcycle(w):
@@ -527,7 +569,10 @@ def main():
     ap.add_argument("--requests", type=int, default=32, help="c5: requests in the stream")
     ap.add_argument("--pool-gb", type=float, default=40.0, help="c5: server pool size")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision and adaptive-tolerance variants")
+    ap.add_argument("--mg-rel", type=float, default=None,
+                    help="headline run: solver tolerance max(mg_tol, MG_REL x sweep residual)")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
@@ -544,6 +589,9 @@ def main():
             print(json.dumps(run_alpha(args)), flush=True)
         return
     w = WORKLOADS[args.workload]
+    if args.mg_rel:
+        w = dict(w, mg_rel=args.mg_rel,
+                 desc=w["desc"] + f"; solves stop at max(mg_tol, {args.mg_rel} x sweep residual)")
     args.steps = args.steps or w["steps"]
     args.warmup = w["warmup"] if args.warmup is None else args.warmup
     if args.warmup < 3 and w["slices"] == 1:
@@ -569,35 +617,11 @@ def main():
     out, ctx, st, u0, uT = run_ours(args, w, rank, world)
 
     if rank == 0 and world == 1 and not args.no_mixed and w["precision"] == "fp64" and w["coarse"]:
-        # the same workload with FP32 V-cycles inside FP64 refinement
-        import torch
-        from paper_1307_7867_gb300 import heat3d as H
-        cm = H.Context(make_cfg(H, w, precision="mixed", graphs=not args.no_graphs),
-                       stream=torch.cuda.Stream())
-        u0_d = torch.from_numpy(u0).cuda()
-        o = torch.empty_like(u0_d)
-        if args.warmup > 0:
-            H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
-            H.pfasst_run(cm, u0_d, o, allow_notconv=True)
-        H.heat3d_set_interval(cm, 0.0, args.steps * w["dt"])
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(cm.stream)
-        rc, sm = H.pfasst_run(cm, u0_d, o, allow_notconv=True)
-        e1.record(cm.stream)
-        torch.cuda.synchronize()
-        s_m = e0.elapsed_time(e1) / 1e3
-        um = o.cpu().numpy()
-        Nf = w["fine"][0]
-        a_pde = analytic_amplitude(args.steps * w["dt"])
-        from paper_1307_7867_gb300 import inputs
-        err_m = float(np.abs(um - a_pde * inputs.sine_mode(Nf)).max() / abs(a_pde))
-        out["mixed"] = {"value": Nf ** 3 * args.steps / s_m, "ms_per_step": s_m * 1e3 / args.steps,
-                        "rel_err_vs_pde_solution": err_m,
-                        "max_rel_diff_vs_fp64": float(np.abs(um - uT).max() / np.abs(uT).max()),
-                        "vcycles": sm["vcycles"], "iters": sm["iters"],
-                        "equal_error": err_m <= 1.01 * out["accuracy"]["rel_err_vs_pde_solution"]}
-        cm.close()
+        # the same workload with FP32 V-cycles inside FP64 refinement, and with
+        # solves whose tolerance follows the sweep's residual
+        out["mixed"] = run_variant(args, w, u0, uT, out, "mixed", 0.0)
+        out["adaptive"] = run_variant(args, w, u0, uT, out, "fp64", ADAPTIVE_REL["fp64"])
+        out["adaptive_mixed"] = run_variant(args, w, u0, uT, out, "mixed", ADAPTIVE_REL["mixed"])
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fv = st["vcycles_level"][0] / max(args.steps, 1)

@@ -66,6 +66,10 @@ typedef struct {
   double tol;     /* stop when max|b - A u| <= tol; tol < 0: exactly max_cycles cycles */
   int inner;      /* V-cycles per refinement step (per FP64 residual), >= 1; the
                      tolerance is checked after each step */
+  double rel;     /* > 0 (with tol >= 0): inside an SDC sweep, item b's solves stop at
+                     max(tol, rel * r_b), r_b = the collocation residual of the sweep's
+                     incoming iterate (the paper leaves the solver tolerance open);
+                     0: the fixed tol */
 } heat3d_mg;
 
 typedef struct {

@@ -51,6 +51,8 @@ typedef struct {
   double mg_tol;  /* stop a solve when max|b - A u| <= mg_tol; < 0: fixed count */
   int mg_max;     /* V-cycle cap per solve */
   int nu1, nu2;   /* pre- and post-smoothing sweeps, V(nu1, nu2) */
+  double mg_rel;  /* > 0: a sweep's solves stop at max(mg_tol, mg_rel * residual of the
+                     sweep's incoming iterate) */
 } or_problem;
 
 typedef struct {
@@ -374,6 +376,9 @@ void or_spread(const or_level* L, const or_problem* P, const double* u0, double*
   or_eval_F_all(L, P, U, F);
 }
 
+double or_sdc_residual(const or_level* L, const or_problem* P, double t0, double dt,
+                       const double* U, const double* F, const double* tauQ);
+
 /* One IMEX-Euler SDC sweep over [t0, t0 + dt] (the sweep equation of
  * Sec. 1.1), U and F updated in place.  tauQ (M fields or NULL) is the FAS
  * correction in cumulative form; the sweep adds tauQ_{m+1} - tauQ_m on the
@@ -385,6 +390,14 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
   size_t n = n3(N);
   double tau[8], S[64];
   if (or_gl_nodes(M, tau) != OR_OK || or_smatrix(M, S) != OR_OK) return OR_EINVAL;
+  /* Inner tolerance of this sweep's solves: fixed, or tied to the collocation
+   * residual of the incoming iterate (the paper leaves the solver tolerance
+   * open; the residual threshold applies to the outer iteration). */
+  double mg_tol = P->mg_tol;
+  if (P->mg_rel > 0 && P->mg_tol >= 0) {
+    double r_in = or_sdc_residual(L, P, t0, dt, U, F, tauQ);
+    if (P->mg_rel * r_in > mg_tol) mg_tol = P->mg_rel * r_in;
+  }
   double* Fold = (double*)malloc((size_t)M * n * sizeof(double));
   double* phi = (double*)malloc(n * sizeof(double));
   double* rhs = (double*)malloc(n * sizeof(double));
@@ -406,7 +419,7 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
     (void)tm1;
     int cyc = 0;
     double res = 0.0;
-    int rc = or_mg_solve(N, L->order, dtm * P->nu, U + (m + 1) * n, rhs, P->mg_tol, P->mg_max,
+    int rc = or_mg_solve(N, L->order, dtm * P->nu, U + (m + 1) * n, rhs, mg_tol, P->mg_max,
                          P->nu1, P->nu2, &cyc, &res);
     if (rc == OR_ENOTCONV) { status = OR_ENOTCONV; if (st) st->notconv++; }
     else if (rc != OR_OK) { status = rc; break; }

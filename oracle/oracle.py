@@ -39,7 +39,8 @@ class Level(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("nu", C.c_double), ("forcing", C.c_int), ("kappa", C.c_double),
-                ("mg_tol", C.c_double), ("mg_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int)]
+                ("mg_tol", C.c_double), ("mg_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("mg_rel", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -217,10 +218,11 @@ class Prob:
     mg_max: int = 50
     nu1: int = 2
     nu2: int = 1
+    mg_rel: float = 0.0
 
     def c(self):
         return Problem(self.nu, self.forcing, self.kappa, self.mg_tol, self.mg_max, self.nu1,
-                       self.nu2)
+                       self.nu2, self.mg_rel)
 
 
 def spread(N, order, M, prob: Prob, u0):

@@ -189,6 +189,8 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
   if (!(cfg->nu > 0) || !(cfg->dt > 0)) return h3d_fail(c, HEAT3D_EINVAL, "nu and dt must be > 0");
   if (cfg->mg.nu1 < 1 || cfg->mg.nu2 < 0 || cfg->mg.max_cycles < 1)
     return h3d_fail(c, HEAT3D_EINVAL, "multigrid needs nu1 >= 1, nu2 >= 0, max_cycles >= 1");
+  if (!(cfg->mg.rel >= 0 && cfg->mg.rel < 1))
+    return h3d_fail(c, HEAT3D_EINVAL, "mg.rel must lie in [0, 1)");
   if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED)
     return h3d_fail(c, HEAT3D_EINVAL, "precision must be HEAT3D_FP64 or HEAT3D_MIXED");
   if (cfg->slices < 1 || cfg->sweeps_fine < 0 || cfg->sweeps_coarse < 0 || cfg->iters < 0)
@@ -634,7 +636,7 @@ static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const 
 template <typename T>
 static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
                       const double* rhs, long long bs, int max_cycles, double tol,
-                      heat3d_stats* s) {
+                      const double* tolv, heat3d_stats* s) {
   SdcLevel& L = c->lv[lev];
   const Grid& g = L.mg[0];
   const int order = L.L.order;
@@ -668,7 +670,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     RET(read_norms(c, L, b0, B, nrm));
     for (int b = 0; b < B; ++b) {
       if (!(nrm[b] <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
-      if (nrm[b] <= tol) { ha[b] = 0; --live; }
+      if (nrm[b] <= (tolv ? tolv[b] : tol)) { ha[b] = 0; --live; }
     }
     if (live < B) CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   }
@@ -711,7 +713,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
       for (int b = 0; b < B; ++b) {
         if (!ha[b]) continue;
         if (!(nrm[b] <= 1e300)) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
-        if (nrm[b] <= tol) { ha[b] = 0; --live; changed = true; }
+        if (nrm[b] <= (tolv ? tolv[b] : tol)) { ha[b] = 0; --live; changed = true; }
       }
       if (changed && live > 0)
         CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
@@ -739,9 +741,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
 }
 
 int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
-                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s) {
-  if (h3d_tsize(c) == 4) return mg_solve_T<float>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, s);
-  return mg_solve_T<double>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, s);
+                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s,
+                 const double* tolv) {
+  if (h3d_tsize(c) == 4)
+    return mg_solve_T<float>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, tolv, s);
+  return mg_solve_T<double>(c, lev, slot, b0, B, u, us, rhs, bs, max_cycles, tol, tolv, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,7 +787,9 @@ int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector
 
 // One sweep over items [b0, b0+B).  When check_tol >= 0 the residual of the
 // incoming iterate is computed by the quadrature kernel first; if it is
-// <= check_tol for every item the sweep is skipped and 1 is returned.
+// <= check_tol for every item the sweep is skipped and 1 is returned.  With
+// mg.rel > 0 (and mg.tol >= 0) the same residual r_b sets item b's solver
+// tolerance for this sweep to max(mg.tol, mg.rel * r_b).
 int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_stats* s) {
   SdcLevel& L = c->lv[lev];
   const int M = L.L.M;
@@ -793,11 +799,14 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
   double* U = L.U + (size_t)b0 * M * fs;
   double* F = L.F + (size_t)b0 * M * fs;
   double* I = L.I + (size_t)b0 * (M - 1) * fs;
-  const bool want = check_tol >= 0;
+  const heat3d_mg& mg = c->cfg.mg;
+  const bool adapt = mg.rel > 0 && mg.tol >= 0;
+  const bool want = check_tol >= 0 || adapt;
   if (want) CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
   CK(launch_integrals(M, L.g, B, U, F, (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
                       I, L.items_d + b0, L.phi, want ? L.norms + b0 : nullptr, nullptr, st));
   c->bytes += 8.0 * pts * (2 * M + (M - 1) + ((lev == 1 && L.has_tau) ? (M - 1) : 0));
+  std::vector<double> tolv;
   if (want) {
     std::vector<double> n;
     RET(read_norms(c, L, b0, B, n));
@@ -807,13 +816,17 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
       mx = std::max(mx, v);
     }
     if (s) s->residual = mx;
-    if (mx <= check_tol) return 1;
+    if (check_tol >= 0 && mx <= check_tol) return 1;
+    if (adapt) {
+      tolv.resize(B);
+      for (int b = 0; b < B; ++b) tolv[b] = std::max(mg.tol, mg.rel * n[b]);
+    }
   }
   int status = HEAT3D_OK;
   for (int m = 0; m + 1 < M; ++m) {
     int rc = h3d_mg_solve(c, lev, m, b0, B, U + (size_t)(m + 1) * fs, (long long)M * fs,
-                          I + (size_t)m * fs, (long long)(M - 1) * fs, c->cfg.mg.max_cycles,
-                          c->cfg.mg.tol, s);
+                          I + (size_t)m * fs, (long long)(M - 1) * fs, mg.max_cycles, mg.tol, s,
+                          adapt ? tolv.data() : nullptr);
     if (rc == HEAT3D_ENOTCONV) status = rc;
     else if (rc < 0) return rc;
     const bool add = m + 1 <= M - 2;
@@ -1140,7 +1153,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->iters = 20;
   cfg->tol_sdc = 1e-10;
   cfg->predictor = 1;
-  cfg->mg = heat3d_mg{2, 1, 50, 1e-10, 1};
+  cfg->mg = heat3d_mg{2, 1, 50, 1e-10, 1, 0.0};
   cfg->precision = HEAT3D_FP64;
   cfg->forcing = HEAT3D_FORCING_PAPER_LITERAL;
   cfg->batch = 1;

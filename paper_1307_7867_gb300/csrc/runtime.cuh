@@ -103,8 +103,10 @@ void h3d_fill_item(heat3d_ctx* c, int lev, int item, double t0);
 int h3d_upload_items(heat3d_ctx* c, int lev, int b0, int B);
 int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* cvals);
 int h3d_set_item_operators(heat3d_ctx* c, int lev, int b0, int B);
+// tolv (optional): per-item tolerances for items [b0, b0+B), replacing tol.
 int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
-                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s);
+                 const double* rhs, long long bs, int max_cycles, double tol, heat3d_stats* s,
+                 const double* tolv = nullptr);
 int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B);
 int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector<double>* per_item);
 int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_stats* s);

@@ -356,7 +356,8 @@ int heat3d_server_create(const heat3d_server_config* cfg, heat3d_server** out) {
   if (!cfg || !out || !cfg->pool || cfg->pool_bytes == 0 || cfg->max_active < 1 || cfg->sweeps < 1)
     return HEAT3D_EINVAL;
   if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED) return HEAT3D_EINVAL;
-  if (cfg->mg.nu1 < 1 || cfg->mg.max_cycles < 1) return HEAT3D_EINVAL;
+  if (cfg->mg.nu1 < 1 || cfg->mg.max_cycles < 1 || !(cfg->mg.rel >= 0 && cfg->mg.rel < 1))
+    return HEAT3D_EINVAL;
   auto* s = new heat3d_server();
   s->cfg = *cfg;
   if (cudaSetDevice(cfg->device) != cudaSuccess ||

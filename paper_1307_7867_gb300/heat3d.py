@@ -48,7 +48,7 @@ class Level(C.Structure):
 
 class MG(C.Structure):
     _fields_ = [("nu1", C.c_int), ("nu2", C.c_int), ("max_cycles", C.c_int), ("tol", C.c_double),
-                ("inner", C.c_int)]
+                ("inner", C.c_int), ("rel", C.c_double)]
 
 
 class Config(C.Structure):
@@ -260,7 +260,7 @@ def pfasst_run(ctx: Context, u0, uT, allow_notconv=False):
 def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2, sweeps_coarse=1,
                 slices=1, iters=20, tol_sdc=1e-10, predictor=1, nu1=2, nu2=1, max_cycles=50,
                 mg_tol=1e-10, precision=FP64, forcing=FORCING_PAPER_LITERAL, batch=1, device=0,
-                use_graphs=0, autotune=1, inner=1, fuse_coarse=1) -> Config:
+                use_graphs=0, autotune=1, inner=1, fuse_coarse=1, mg_rel=0.0) -> Config:
     """fine, coarse: (N, order, M) tuples; coarse None gives single-level SDC."""
     cfg = heat3d_config_default()
     cfg.nu, cfg.T, cfg.dt = nu, T, dt
@@ -270,7 +270,7 @@ def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2,
         cfg.levels[1] = Level(*coarse)
     cfg.sweeps_fine, cfg.sweeps_coarse = sweeps_fine, sweeps_coarse
     cfg.slices, cfg.iters, cfg.tol_sdc, cfg.predictor = slices, iters, tol_sdc, predictor
-    cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner)
+    cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner, mg_rel)
     cfg.precision, cfg.forcing, cfg.batch, cfg.device = precision, forcing, batch, device
     cfg.use_graphs = use_graphs
     cfg.autotune = autotune
@@ -317,14 +317,14 @@ class Server:
     """Continuous-batching server (heat3d_server_*) over a torch-allocated pool."""
 
     def __init__(self, pool, max_active=8, sweeps=4, precision=FP64, mg_tol=1e-10,
-                 max_cycles=50, nu1=2, nu2=1, inner=1, device=0):
+                 max_cycles=50, nu1=2, nu2=1, inner=1, device=0, mg_rel=0.0):
         self.pool = pool  # keep the memory alive
         cfg = ServerConfig()
         cfg.device = device
         cfg.pool = C.c_void_p(pool.data_ptr())
         cfg.pool_bytes = pool.numel() * pool.element_size()
         cfg.max_active, cfg.sweeps, cfg.precision = max_active, sweeps, precision
-        cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner)
+        cfg.mg = MG(nu1, nu2, max_cycles, mg_tol, inner, mg_rel)
         h = C.c_void_p()
         rc = load().heat3d_server_create(C.byref(cfg), C.byref(h))
         if rc != OK:

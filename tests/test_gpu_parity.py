@@ -203,6 +203,47 @@ def test_run_mlsdc_small(H, oracle):
     assert rel(uT, ref) <= 1e-11
 
 
+@pytest.mark.parametrize("mg_rel", [0.01, 0.1])
+def test_run_mlsdc_adaptive_inner_tolerance(H, oracle, mg_rel):
+    """Per-item solver tolerance max(mg_tol, mg_rel x incoming collocation
+    residual), on both levels: same iterations and V-cycles as the oracle."""
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
+                        mg_tol=1e-12, mg_rel=mg_rel)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(31, seed=4, kmax=5)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, orc, ost = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-12, mg_rel=mg_rel), 1 / 64,
+                                     2, u0, nsweeps_fine=2, max_iters=20, tol=1e-10)
+    assert st["iters"] == ost["iters"] and st["vcycles"] == ost["vcycles"]
+    assert rel(uT, ref) <= 1e-11
+
+
+def test_adaptive_inner_tolerance_mixed_and_batched(H, oracle):
+    """Mixed precision with the adaptive tolerance, PFASST with two slices in
+    one batch, iterated to residual 1e-11: the result matches the converged
+    FP64 oracle to 1e-9."""
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, sweeps_fine=1, slices=2, iters=40,
+                        tol_sdc=1e-11, mg_tol=1e-12, mg_rel=0.05, precision=H.MIXED, inner=2)
+    ctx = H.Context(cfg)
+    u0 = inputs.sine_mode(31)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, _, ost = oracle.pfasst_run(fine, coarse, oracle.Prob(mg_tol=1e-12, mg_rel=0.05), 1 / 32,
+                                    2, 2, u0, nsweeps_fine=1, max_iters=40, tol=1e-11)
+    assert st["residual"] <= 1e-11 and ost["residual"] <= 1e-11
+    assert rel(uT, ref) <= 1e-9
+
+
+def test_adaptive_tolerance_rejects_bad_rel(H):
+    for bad in (-0.1, 1.0, float("nan")):
+        cfg = H.make_config((15, 2, 3), dt=1 / 8, T=1 / 8, mg_rel=bad)
+        with pytest.raises(H.Heat3DError):
+            H.Context(cfg)
+
+
 @pytest.mark.parametrize("P,K", [(4, 3), (8, 2)])
 def test_run_pfasst_small(H, oracle, P, K):
     fine, coarse = (15, 4, 5), (7, 2, 3)

@@ -178,6 +178,22 @@ def test_mlsdc_converges_to_sdc_collocation(oracle):
     assert np.abs(a - b).max() <= 1e-10
 
 
+def test_adaptive_inner_tolerance_keeps_the_collocation_solution(oracle):
+    """Solving each substep only to rel x (incoming collocation residual) leaves
+    the fixed point alone: MLSDC converged to 1e-12 still reaches the strict
+    SDC collocation solution, with fewer V-cycles than fixed-tolerance solves."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    strict = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    loose = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100, mg_rel=0.05)
+    u0 = inputs.sine_mode(15)
+    a, rc, sa = oracle.mlsdc_run(fine, coarse, loose, 1 / 16, 2, u0, max_iters=60, tol=1e-12)
+    b, rc2, _ = oracle.sdc_run(*fine, strict, 1 / 16, 2, 60, u0, tol=1e-12)
+    c, rc3, sc = oracle.mlsdc_run(fine, coarse, strict, 1 / 16, 2, u0, max_iters=60, tol=1e-12)
+    assert rc == rc2 == rc3 == oracle.OK
+    assert np.abs(a - b).max() <= 1e-10
+    assert sa["vcycles"] < sc["vcycles"]
+
+
 def test_pfasst_single_slice_is_mlsdc(oracle):
     """PFASST on one time slice is MLSDC (Sec. 2.1)."""
     fine, coarse = (7, 4, 5), (3, 2, 3)
