@@ -12,7 +12,10 @@ namespace h3d {
 // kind: 0 automatic (tiled for N >= 32, else z-march), 1 z-march (one column
 // per thread), 2 shared-memory tile 32 x 8 (128 threads, 2 rows each), 3 tile
 // 32 x 16 (256 threads, 2 rows each), 4 tile 32 x 16 (128 threads, 4 rows
-// each), 5 and 6 as 2 and 3 with 6 planes of prefetch instead of 3; zc:
+// each), 5 and 6 as 2 and 3 with 6 planes of prefetch instead of 3; FP32
+// Jacobi and residual only: four x points per thread, tile 128 x TY: 7 (4
+// warps x 2 rows), 8 (8 warps x 1 row), 9 (4 warps x 4 rows), 10 (8 warps x
+// 2 rows), other operators take kind 3 for these; zc:
 // planes per block along z.
 struct Shape {
   int kind = 0;

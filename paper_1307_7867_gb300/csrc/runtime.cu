@@ -1029,12 +1029,13 @@ static bool tune_log() {
   return v && v[0] == '1';
 }
 
-static std::vector<Shape> shape_candidates(int N) {
+// vec4: the operator has the four-points-per-thread FP32 tile (kinds 7-10).
+static std::vector<Shape> shape_candidates(int N, bool vec4) {
   std::vector<Shape> v;
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
     if (zc <= N) v.push_back(Shape{1, zc});
   if (N >= 16)
-    for (int kind = 2; kind <= 6; ++kind)
+    for (int kind = 2; kind <= (vec4 ? 10 : 6); ++kind)
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
   return v;
@@ -1052,7 +1053,7 @@ static int autotune_T(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1) {
       T* t = mgbuf<T>(L, k, 2, 0);
       float best = 1e30f;
       Shape pick{1, std::min(16, g.N)};
-      for (Shape sh : shape_candidates(g.N)) {
+      for (Shape sh : shape_candidates(g.N, sizeof(T) == 4)) {
         float ms = time_shape(c, e0, e1, [&] {
           return launch_jacobi<T>(L.L.order, g, L.B, e, b, t, nullptr, 0, cf, nullptr, sh, c->st);
         });
@@ -1066,7 +1067,7 @@ static int autotune_T(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1) {
     float best = 1e30f;
     Shape pick{1, std::min(16, L.g.N)};
     const long long fs = L.g.fs;
-    for (Shape sh : shape_candidates(L.g.N)) {
+    for (Shape sh : shape_candidates(L.g.N, false)) {
       float ms = time_shape(c, e0, e1, [&] {
         return launch_lap(L.L.order, L.g, L.B, L.U, (long long)L.L.M * fs, L.F, (long long)L.L.M * fs,
                           L.alpha_items, nullptr, nullptr, 0, nullptr, sh, c->st);
@@ -1215,6 +1216,19 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   CK(cudaStreamSynchronize(c->st));
   c->bound = true;
   if (c->cfg.autotune) RET(h3d_autotune(c));
+  // HEAT3D_SHAPE=kind,zc forces one launch shape on every stencil (testing:
+  // every shape must give bitwise the same results)
+  if (const char* f = getenv("HEAT3D_SHAPE")) {
+    int kind = 0, zc = 0;
+    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 10 && zc >= 1) {
+      for (int l = 0; l < c->cfg.nlevels; ++l) {
+        SdcLevel& L = c->lv[l];
+        for (int k = 0; k < L.nmg; ++k)
+          if (kind == 1 || L.mg[k].N >= 16) L.shapeT[k] = Shape{kind, zc};
+        if (kind == 1 || L.g.N >= 16) L.shape64 = Shape{kind, zc};
+      }
+    }
+  }
   return HEAT3D_OK;
 }
 

@@ -8,9 +8,11 @@
 //    (z-R .. z+R, R = 1 or 2) live in a shared-memory ring that cp.async
 //    fills D planes ahead in 16-byte chunks, so HBM streams while the block
 //    computes; every neighbour is read from shared memory and each thread
-//    computes RY rows (independent FP64 chains for the FP64 pipe).  Cells of
-//    the tile halo that fall outside the domain are written with plain loads
-//    under the boundary rule.
+//    computes RY rows (independent FP64 chains for the FP64 pipe).  Cells
+//    outside the domain are never loaded: the few points next to a boundary
+//    replace those neighbours in registers (fix_axis).
+//  * k_tile4 (FP32 Jacobi and residual): as k_tile with four x points per
+//    thread and 16-byte shared and global accesses.
 //  * k_zmarch (small grids): one (x, y) column per thread, z-neighbours in a
 //    register queue, x/y neighbours through L1.
 // Boundary rule of every stencil read: indices -1 and N are the Dirichlet
@@ -23,6 +25,8 @@
 // outputs from the centre u, the sum s1 of the 6 nearest and s2 of the 6
 // second neighbours, and returns the value whose max |.| is accumulated when
 // the launch asks for a norm.
+#include <type_traits>
+
 #include "kernels.cuh"
 
 namespace h3d {
@@ -55,12 +59,21 @@ __device__ __forceinline__ T at(const T* __restrict__ u, const Grid& g, int i, i
   return neg ? -v : v;
 }
 
-// As at(), and 0 for indices beyond the ghost layer (never used by a stencil).
-template <typename T>
-__device__ __forceinline__ T at_any(const T* __restrict__ u, const Grid& g, int i, int j, int k) {
-  const int N = g.N;
-  if (i < -2 || i > N + 1 || j < -2 || j > N + 1 || k < -2 || k > N + 1) return T(0);
-  return at(u, g, i, j, k);
+// The boundary rule for the neighbours, along one axis, of a point at
+// coordinate p of that axis (the tiled kernels never load cells outside the
+// domain; their ring slots hold stale data and are replaced here): indices -1
+// and N read 0, the wide stencil's ghosts -2 and N+1 read minus the point
+// itself (they occur only for p = 0 and p = N - 1).
+template <typename T, int R>
+__device__ __forceinline__ void fix_axis(int p, int N, T c, T& m1, T& p1, T& m2, T& p2) {
+  if (p == 0) m1 = T(0);
+  if (p == N - 1) p1 = T(0);
+  if (R == 2) {
+    if (p == 0) m2 = -c;
+    else if (p == 1) m2 = T(0);
+    if (p == N - 1) p2 = -c;
+    else if (p == N - 2) p2 = T(0);
+  }
 }
 
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
@@ -205,6 +218,49 @@ struct OpJacobi {
     else o_[idx] = v;
     return 0.0;
   }
+  // Four consecutive x points (FP32 storage, k_tile4): idx is a multiple of
+  // 4, n >= 1 of the four are inside the grid.  Same arithmetic per point as
+  // apply().
+  static constexpr bool kVec4 = sizeof(TT) == 4;
+  struct Ex4 { float4 r; double2 u01, u23; };
+  __device__ Ex4 load4(int idx) const {
+    Ex4 x;
+    x.r = *reinterpret_cast<const float4*>(r_ + idx);
+    if (UPD) {
+      x.u01 = *reinterpret_cast<const double2*>(u_ + idx);
+      x.u23 = *reinterpret_cast<const double2*>(u_ + idx + 2);
+    }
+    return x;
+  }
+  __device__ void apply4(int idx, int n, const float (&c)[4], const float (&s1)[4],
+                         const float (&s2)[4], const Ex4& ex) {
+    const float rr[4] = {ex.r.x, ex.r.y, ex.r.z, ex.r.w};
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float S = combine<float, ORDER>(s1[q], s2[q]);
+      float res = fmaf(-d, c[q], fmaf(ec, S, rr[q]));
+      v[q] = fmaf(wd, res, c[q]);
+    }
+    if (UPD) {
+      const double w[4] = {ex.u01.x + (double)v[0], ex.u01.y + (double)v[1],
+                           ex.u23.x + (double)v[2], ex.u23.y + (double)v[3]};
+      if (n >= 4) {
+        *reinterpret_cast<double2*>(u_ + idx) = make_double2(w[0], w[1]);
+        *reinterpret_cast<double2*>(u_ + idx + 2) = make_double2(w[2], w[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < n) u_[idx + q] = w[q];
+      }
+    } else if (n >= 4) {
+      *reinterpret_cast<float4*>(o_ + idx) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < n) o_[idx + q] = v[q];
+    }
+  }
 };
 
 // rr = r - A e
@@ -229,6 +285,26 @@ struct OpResid {
     T S = combine<T, ORDER>(s1, s2);
     o_[idx] = fma(-d, c, fma(ec, S, ex.r));
     return 0.0;
+  }
+  static constexpr bool kVec4 = sizeof(TT) == 4;
+  struct Ex4 { float4 r; };
+  __device__ Ex4 load4(int idx) const { return Ex4{*reinterpret_cast<const float4*>(r_ + idx)}; }
+  __device__ void apply4(int idx, int n, const float (&c)[4], const float (&s1)[4],
+                         const float (&s2)[4], const Ex4& ex) {
+    const float rr[4] = {ex.r.x, ex.r.y, ex.r.z, ex.r.w};
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float S = combine<float, ORDER>(s1[q], s2[q]);
+      v[q] = fmaf(-d, c[q], fmaf(ec, S, rr[q]));
+    }
+    if (n >= 4) {
+      *reinterpret_cast<float4*>(o_ + idx) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < n) o_[idx + q] = v[q];
+    }
   }
 };
 
@@ -316,38 +392,29 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   const T* __restrict__ u = o.src(b);
   const int tid = threadIdx.y * 32 + threadIdx.x;
 
-  // Plane z into ring slot `slot`: interior 16-byte chunks by cp.async, the
-  // rest (domain halo, ghost planes) by plain loads under the boundary rule.
+  // Plane z into ring slot `slot` by 16-byte cp.async chunks.  Only chunks of
+  // rows and planes inside the domain whose 16 bytes lie within the allocated
+  // row (x < px) are copied; the stencil replaces every neighbour outside the
+  // domain by the boundary rule (fix_axis), so nothing else is ever read.
   // A thread's chunks are the same for every plane: offsets computed once.
   constexpr int NCH = (SY * CH + NT - 1) / NT;
-  int soff[NCH], cgx[NCH], cgy[NCH], goff[NCH];
-  bool fast[NCH];
+  int soff[NCH], goff[NCH];
 #pragma unroll
   for (int q = 0; q < NCH; ++q) {
     const int c = tid + q * NT;
     const int ry = c / CH, cx = c - ry * CH;
-    cgy[q] = y0 - R + ry;
-    cgx[q] = x0 - XH + cx * XH;
-    soff[q] = c < SY * CH ? ry * SX + cx * XH : -1;
-    goff[q] = cgy[q] * g.px + cgx[q];
-    fast[q] = cgy[q] >= 0 && cgy[q] < N && cgx[q] >= 0 && cgx[q] + XH <= N;
+    const int cgy = y0 - R + ry, cgx = x0 - XH + cx * XH;
+    const bool ok = c < SY * CH && cgy >= 0 && cgy < N && cgx >= 0 && cgx + XH <= g.px;
+    soff[q] = ok ? ry * SX + cx * XH : -1;
+    goff[q] = cgy * g.px + cgx;
   }
   auto issue = [&](int z, int slot) {
-    if (z <= z1 - 1 + R) {
+    if (z >= 0 && z < N && z <= z1 - 1 + R) {
       T* dst = ring + slot * PS;
-      const bool zin = z >= 0 && z < N;
       const T* uz = u + z * plane;
 #pragma unroll
-      for (int q = 0; q < NCH; ++q) {
-        if (soff[q] < 0) continue;
-        T* d = dst + soff[q];
-        if (zin && fast[q]) {
-          cp_async16(d, uz + goff[q]);
-        } else {
-#pragma unroll
-          for (int e = 0; e < XH; ++e) d[e] = at_any(u, g, cgx[q] + e, cgy[q], z);
-        }
-      }
+      for (int q = 0; q < NCH; ++q)
+        if (soff[q] >= 0) cp_async16(dst + soff[q], uz + goff[q]);
     }
     cp_async_commit();
   };
@@ -358,6 +425,7 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
   const int i = x0 + tx;
   const int jb = y0 + ty * RY;
   const int sbase = (R + ty * RY) * SX + XH + tx;
+  const bool xedge = i < R || i >= N - R;
   int idx0 = z0 * plane + jb * g.px + i;
   int cs = R;                // ring slot of plane k
   int fs_ = 2 * R + D;       // slot that receives plane k + R + D
@@ -380,15 +448,26 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
     const T* Pp1 = ring + sp1 * PS + sbase;
     const T* Pm2 = ring + sm2 * PS + sbase;
     const T* Pp2 = ring + sp2 * PS + sbase;
+    const bool zedge = k < R || k >= N - R;
 #pragma unroll
     for (int r = 0; r < RY; ++r) {
       const int o0 = r * SX;
+      const int j = jb + r;
       const T c = P0[o0];
-      T s1 = ((P0[o0 - 1] + P0[o0 + 1]) + (P0[o0 - SX] + P0[o0 + SX])) + (Pm1[o0] + Pp1[o0]);
+      T xm1 = P0[o0 - 1], xp1 = P0[o0 + 1], ym1 = P0[o0 - SX], yp1 = P0[o0 + SX];
+      T zm1 = Pm1[o0], zp1 = Pp1[o0];
+      T xm2 = T(0), xp2 = T(0), ym2 = T(0), yp2 = T(0), zm2 = T(0), zp2 = T(0);
+      if (R == 2) {
+        xm2 = P0[o0 - 2]; xp2 = P0[o0 + 2]; ym2 = P0[o0 - 2 * SX]; yp2 = P0[o0 + 2 * SX];
+        zm2 = Pm2[o0]; zp2 = Pp2[o0];
+      }
+      if (xedge) fix_axis<T, R>(i, N, c, xm1, xp1, xm2, xp2);
+      if (j < R || j >= N - R) fix_axis<T, R>(j, N, c, ym1, yp1, ym2, yp2);
+      if (zedge) fix_axis<T, R>(k, N, c, zm1, zp1, zm2, zp2);
+      T s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
       T s2 = T(0);
-      if (R == 2)
-        s2 = ((P0[o0 - 2] + P0[o0 + 2]) + (P0[o0 - 2 * SX] + P0[o0 + 2 * SX])) + (Pm2[o0] + Pp2[o0]);
-      if (i < N && jb + r < N) {
+      if (R == 2) s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
+      if (i < N && j < N) {
         double rv = o.apply(idx0 + r * g.px, c, s1, s2, ex[r]);
         if (NORM) {
           unsigned long long bits = abs_bits(rv);
@@ -424,6 +503,187 @@ cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active
   return cudaSuccess;
 }
 
+// FP32 tile with four x points per thread: a warp covers 128 consecutive x
+// points of one row, so every neighbour read is a 16-byte (centre, y, z) or
+// 8-byte (x halo) shared-memory access shared by four points, and the
+// per-point loads and stores are float4.  Ring and loader as k_tile (the
+// 16-byte x halo is exactly one chunk).  The sums per point are formed in the
+// same order as k_tile and k_zmarch, so the results are bitwise identical.
+template <int ORDER, int TYT, int RY, int D, typename Op>
+__global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, const int* active, Op op) {
+  using T = typename Op::T;
+  static_assert(sizeof(T) == 4, "k_tile4 is the FP32 path");
+  constexpr int R = ORDER == 2 ? 1 : 2;
+  constexpr int TX = 128, TY = TYT * RY;
+  constexpr int XH = 4;
+  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D + 1;
+  constexpr int CH = SX / XH;
+  constexpr int NT = 32 * TYT;
+  constexpr int PS = SY * SX;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  const int b = blockIdx.z / nzc;
+  if (active && !active[b]) return;  // uniform over the block
+  const int N = g.N;
+  const int plane = (int)g.plane;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = (blockIdx.z - b * nzc) * zc, z1 = min(N, z0 + zc);
+  Op o = op;
+  o.init(b);
+  const float* __restrict__ u = o.src(b);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+
+  constexpr int NCH = (SY * CH + NT - 1) / NT;
+  int soff[NCH], goff[NCH];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) {
+    const int c = tid + q * NT;
+    const int ry = c / CH, cx = c - ry * CH;
+    const int cgy = y0 - R + ry, cgx = x0 - XH + cx * XH;
+    const bool ok = c < SY * CH && cgy >= 0 && cgy < N && cgx >= 0 && cgx + XH <= g.px;
+    soff[q] = ok ? ry * SX + cx * XH : -1;
+    goff[q] = cgy * g.px + cgx;
+  }
+  auto issue = [&](int z, int slot) {
+    if (z >= 0 && z < N && z <= z1 - 1 + R) {
+      float* dst = ring + slot * PS;
+      const float* uz = u + z * plane;
+#pragma unroll
+      for (int q = 0; q < NCH; ++q)
+        if (soff[q] >= 0) cp_async16(dst + soff[q], uz + goff[q]);
+    }
+    cp_async_commit();
+  };
+
+#pragma unroll 1
+  for (int q = 0; q < 2 * R + D; ++q) issue(z0 - R + q, q);
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = x0 + 4 * tx;
+  const int jb = y0 + ty * RY;
+  const int sbase = (R + ty * RY) * SX + XH + 4 * tx;
+  const int nx = N - i;  // points of the thread's four inside the grid
+  const bool xedge = i < R || i + 3 >= N - R;
+  int idx0 = z0 * plane + jb * g.px + i;
+  int cs = R;
+  int fs_ = 2 * R + D;
+  for (int k = z0; k < z1; ++k, idx0 += plane) {
+    typename Op::Ex4 ex[RY];
+#pragma unroll
+    for (int r = 0; r < RY; ++r)
+      if (nx > 0 && jb + r < N) ex[r] = o.load4(idx0 + r * g.px);
+    cp_async_wait<D - 1>();
+    __syncthreads();
+    issue(k + R + D, fs_);
+    fs_ = ring_next(fs_, NB);
+    const int sm1 = ring_prev(cs, NB), sp1 = ring_next(cs, NB);
+    const int sm2 = ring_prev(sm1, NB), sp2 = ring_next(sp1, NB);
+    const float* P0 = ring + cs * PS + sbase;
+    const float* Pm1 = ring + sm1 * PS + sbase;
+    const float* Pp1 = ring + sp1 * PS + sbase;
+    const float* Pm2 = ring + sm2 * PS + sbase;
+    const float* Pp2 = ring + sp2 * PS + sbase;
+    // centre float4 of rows jb - R .. jb + RY - 1 + R in plane k
+    float4 col[RY + 2 * R];
+#pragma unroll
+    for (int q = 0; q < RY + 2 * R; ++q) col[q] = *reinterpret_cast<const float4*>(P0 + (q - R) * SX);
+    const bool zedge = k < R || k >= N - R;
+#pragma unroll
+    for (int r = 0; r < RY; ++r) {
+      const int o0 = r * SX;
+      const int j = jb + r;
+      const float4 cc = col[r + R];
+      const float c[4] = {cc.x, cc.y, cc.z, cc.w};
+      // x: a[2..3] = x-2, x-1; a[4..7] = the four points; a[8..9] = x+4, x+5
+      float a[10];
+      if (R == 2) {
+        const float2 lh = *reinterpret_cast<const float2*>(P0 + o0 - 2);
+        const float2 rh = *reinterpret_cast<const float2*>(P0 + o0 + 4);
+        a[2] = lh.x; a[3] = lh.y; a[8] = rh.x; a[9] = rh.y;
+      } else {
+        a[2] = 0.f; a[3] = P0[o0 - 1]; a[8] = P0[o0 + 4]; a[9] = 0.f;
+      }
+      a[4] = c[0]; a[5] = c[1]; a[6] = c[2]; a[7] = c[3];
+      const float4 ym1 = col[r + R - 1], yp1 = col[r + R + 1];
+      const float4 zm1 = *reinterpret_cast<const float4*>(Pm1 + o0);
+      const float4 zp1 = *reinterpret_cast<const float4*>(Pp1 + o0);
+      float xm1v[4], xp1v[4], ym1v[4] = {ym1.x, ym1.y, ym1.z, ym1.w}, yp1v[4] = {yp1.x, yp1.y, yp1.z, yp1.w};
+      float zm1v[4] = {zm1.x, zm1.y, zm1.z, zm1.w}, zp1v[4] = {zp1.x, zp1.y, zp1.z, zp1.w};
+      float xm2v[4] = {0.f, 0.f, 0.f, 0.f}, xp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float ym2v[4] = {0.f, 0.f, 0.f, 0.f}, yp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float zm2v[4] = {0.f, 0.f, 0.f, 0.f}, zp2v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xm1v[q] = a[3 + q];
+        xp1v[q] = a[5 + q];
+      }
+      if (R == 2) {
+        const float4 ym2 = col[r + R - 2], yp2 = col[r + R + 2];
+        const float4 zm2 = *reinterpret_cast<const float4*>(Pm2 + o0);
+        const float4 zp2 = *reinterpret_cast<const float4*>(Pp2 + o0);
+        ym2v[0] = ym2.x; ym2v[1] = ym2.y; ym2v[2] = ym2.z; ym2v[3] = ym2.w;
+        yp2v[0] = yp2.x; yp2v[1] = yp2.y; yp2v[2] = yp2.z; yp2v[3] = yp2.w;
+        zm2v[0] = zm2.x; zm2v[1] = zm2.y; zm2v[2] = zm2.z; zm2v[3] = zm2.w;
+        zp2v[0] = zp2.x; zp2v[1] = zp2.y; zp2v[2] = zp2.z; zp2v[3] = zp2.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          xm2v[q] = a[2 + q];
+          xp2v[q] = a[6 + q];
+        }
+      }
+      if (xedge) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(i + q, N, c[q], xm1v[q], xp1v[q], xm2v[q], xp2v[q]);
+      }
+      if (j < R || j >= N - R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(j, N, c[q], ym1v[q], yp1v[q], ym2v[q], yp2v[q]);
+      }
+      if (zedge) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(k, N, c[q], zm1v[q], zp1v[q], zm2v[q], zp2v[q]);
+      }
+      float s1[4], s2[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s1[q] = ((xm1v[q] + xp1v[q]) + (ym1v[q] + yp1v[q])) + (zm1v[q] + zp1v[q]);
+        s2[q] = R == 2 ? ((xm2v[q] + xp2v[q]) + (ym2v[q] + yp2v[q])) + (zm2v[q] + zp2v[q]) : 0.f;
+      }
+      if (nx > 0 && j < N) o.apply4(idx0 + r * g.px, nx, c, s1, s2, ex[r]);
+    }
+    cs = sp1;
+  }
+  cp_async_wait<0>();
+}
+
+template <typename T, int ORDER, int TYT, int RY, int D>
+constexpr int tile4_smem_bytes() {
+  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) * (128 + 8) * 4;
+}
+
+template <int ORDER, int TYT, int RY, int D, typename Op>
+cudaError_t launch_tile4(const Grid& g, int B, int nzc, int zc, const int* active, const Op& op,
+                         cudaStream_t st) {
+  constexpr int smem = tile4_smem_bytes<float, ORDER, TYT, RY, D>();
+  if (smem > 48 * 1024) {
+    static bool set = false;
+    if (!set) {
+      cudaError_t e = cudaFuncSetAttribute(k_tile4<ORDER, TYT, RY, D, Op>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      set = true;
+    }
+  }
+  dim3 blk(32, TYT, 1);
+  dim3 grd((g.N + 127) / 128, (g.N + TYT * RY - 1) / (TYT * RY), nzc * B);
+  k_tile4<ORDER, TYT, RY, D, Op><<<grd, blk, smem, st>>>(g, nzc, zc, active, op);
+  return cudaSuccess;
+}
+
+template <typename Op, typename = void>
+struct has_vec4 : std::false_type {};
+template <typename Op>
+struct has_vec4<Op, std::void_t<decltype(Op::kVec4)>> : std::integral_constant<bool, Op::kVec4> {};
+
 template <int ORDER, bool NORM, typename Op>
 cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long long* norm_bits,
                         const Op& op, Shape sh, cudaStream_t st) {
@@ -445,6 +705,15 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
     case 4: e = launch_tile<ORDER, 4, 4, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
     case 5: e = launch_tile<ORDER, 4, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
     case 6: e = launch_tile<ORDER, 8, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
+    case 7: case 8: case 9: case 10:
+      if constexpr (has_vec4<Op>::value && !NORM) {
+        if (kind == 7) e = launch_tile4<ORDER, 4, 2, 3>(g, B, nzc, zc, active, op, st);
+        else if (kind == 8) e = launch_tile4<ORDER, 8, 1, 3>(g, B, nzc, zc, active, op, st);
+        else if (kind == 9) e = launch_tile4<ORDER, 4, 4, 3>(g, B, nzc, zc, active, op, st);
+        else e = launch_tile4<ORDER, 8, 2, 3>(g, B, nzc, zc, active, op, st);
+        break;
+      }
+      [[fallthrough]];
     default: e = launch_tile<ORDER, 8, 2, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
   }
   if (e != cudaSuccess) return e;

@@ -295,6 +295,38 @@ def test_graphs_and_autotune_change_nothing(H, oracle, precision):
         assert rel(outs[1][0], ref) <= 1e-11
 
 
+SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (8, 2), (9, 16), (10, 64)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_launch_shape_is_bitwise_identical(H, oracle, precision, monkeypatch):
+    """Every stencil launch shape (z-march, the 32-wide tiles, the FP32
+    four-points-per-thread tiles) forced on all grids with N >= 16 gives
+    bitwise the result of the default shapes: PFASST with two slices batched
+    (items in one launch), fine 127^3 (a ragged last x group of 3 points)."""
+    fine, coarse = (127, 4, 3), (63, 2, 3)
+    prec = H.FP64 if precision == "fp64" else H.MIXED
+
+    def run():
+        cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, sweeps_fine=1, slices=2, iters=2,
+                            tol_sdc=-1.0, mg_tol=1e-10, precision=prec, autotune=0,
+                            inner=2 if prec == H.MIXED else 1)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.smooth_random_field(127, seed=11, kmax=6)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        ctx.close()
+        return uT, st["vcycles"]
+
+    monkeypatch.delenv("HEAT3D_SHAPE", raising=False)
+    ref, vref = run()
+    for kind, zc in SHAPES:
+        monkeypatch.setenv("HEAT3D_SHAPE", f"{kind},{zc}")
+        uT, v = run()
+        assert np.array_equal(uT, ref) and v == vref, (kind, zc)
+    monkeypatch.delenv("HEAT3D_SHAPE")
+
+
 def test_graph_replay_counts_launches_and_profile(H):
     """Launch counter and the kernel profile include graph replays."""
     N = 63
