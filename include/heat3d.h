@@ -94,7 +94,7 @@ typedef struct {
                                non-default stream; ignored on the legacy stream) */
   int autotune;             /* 1: time the stencil launch shapes of every multigrid level at
                                heat3d_bind_workspace and keep the fastest (results identical).
-                               The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-10,
+                               The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-14,
                                planes per block zc) forces one shape on every stencil of
                                grids with N >= 16 instead (testing) */
   int fuse_coarse;          /* 1: run the multigrid levels with N <= 15 of a V-cycle in one

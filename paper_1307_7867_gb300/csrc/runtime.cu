@@ -1035,7 +1035,7 @@ static std::vector<Shape> shape_candidates(int N, bool vec4) {
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
     if (zc <= N) v.push_back(Shape{1, zc});
   if (N >= 16)
-    for (int kind = 2; kind <= (vec4 ? 10 : 6); ++kind)
+    for (int kind = 2; kind <= (vec4 ? 14 : 6); ++kind)
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
   return v;
@@ -1220,7 +1220,7 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   // every shape must give bitwise the same results)
   if (const char* f = getenv("HEAT3D_SHAPE")) {
     int kind = 0, zc = 0;
-    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 10 && zc >= 1) {
+    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 14 && zc >= 1) {
       for (int l = 0; l < c->cfg.nlevels; ++l) {
         SdcLevel& L = c->lv[l];
         for (int k = 0; k < L.nmg; ++k)

@@ -89,8 +89,7 @@ __device__ __forceinline__ void warp_max_to(unsigned long long v, unsigned long 
   if ((threadIdx.x & 31) == 0 && v != 0ull) atomicMax(dst, v);
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+__device__ __forceinline__ void cp_async16(unsigned s, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -222,6 +221,7 @@ struct OpJacobi {
   // 4, n >= 1 of the four are inside the grid.  Same arithmetic per point as
   // apply().
   static constexpr bool kVec4 = sizeof(TT) == 4;
+  static constexpr int kRegFloor = UPD ? 96 : 64;  // registers k_tile4 keeps without spilling
   struct Ex4 { float4 r; double2 u01, u23; };
   __device__ Ex4 load4(int idx) const {
     Ex4 x;
@@ -287,6 +287,7 @@ struct OpResid {
     return 0.0;
   }
   static constexpr bool kVec4 = sizeof(TT) == 4;
+  static constexpr int kRegFloor = 64;
   struct Ex4 { float4 r; };
   __device__ Ex4 load4(int idx) const { return Ex4{*reinterpret_cast<const float4*>(r_ + idx)}; }
   __device__ void apply4(int idx, int n, const float (&c)[4], const float (&s1)[4],
@@ -408,13 +409,14 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
     soff[q] = ok ? ry * SX + cx * XH : -1;
     goff[q] = cgy * g.px + cgx;
   }
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   auto issue = [&](int z, int slot) {
     if (z >= 0 && z < N && z <= z1 - 1 + R) {
-      T* dst = ring + slot * PS;
+      const unsigned dst = ring_s + (unsigned)(slot * PS) * (unsigned)sizeof(T);
       const T* uz = u + z * plane;
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
-        if (soff[q] >= 0) cp_async16(dst + soff[q], uz + goff[q]);
+        if (soff[q] >= 0) cp_async16(dst + (unsigned)soff[q] * (unsigned)sizeof(T), uz + goff[q]);
     }
     cp_async_commit();
   };
@@ -509,8 +511,23 @@ cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active
 // per-point loads and stores are float4.  Ring and loader as k_tile (the
 // 16-byte x halo is exactly one chunk).  The sums per point are formed in the
 // same order as k_tile and k_zmarch, so the results are bitwise identical.
+template <int ORDER, int TYT, int RY, int D>
+constexpr int tile4_smem() {
+  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) * (128 + 8) * 4;
+}
+// Blocks per SM that the ring allows, but no more than keeps the operator's
+// register floor (kRegFloor) available: the register cap that keeps them
+// resident together.
+template <int ORDER, int TYT, int RY, int D, int REGS>
+constexpr int tile4_min_blocks() {
+  return (232448 / tile4_smem<ORDER, TYT, RY, D>()) < (65536 / (32 * TYT * REGS))
+             ? (232448 / tile4_smem<ORDER, TYT, RY, D>())
+             : (65536 / (32 * TYT * REGS));
+}
+
 template <int ORDER, int TYT, int RY, int D, typename Op>
-__global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, const int* active, Op op) {
+__global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D, Op::kRegFloor>()))
+    k_tile4(Grid g, int nzc, int zc, const int* active, Op op) {
   using T = typename Op::T;
   static_assert(sizeof(T) == 4, "k_tile4 is the FP32 path");
   constexpr int R = ORDER == 2 ? 1 : 2;
@@ -544,13 +561,14 @@ __global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, con
     soff[q] = ok ? ry * SX + cx * XH : -1;
     goff[q] = cgy * g.px + cgx;
   }
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
   auto issue = [&](int z, int slot) {
     if (z >= 0 && z < N && z <= z1 - 1 + R) {
-      float* dst = ring + slot * PS;
+      const unsigned dst = ring_s + (unsigned)(slot * PS) * 4u;
       const float* uz = u + z * plane;
 #pragma unroll
       for (int q = 0; q < NCH; ++q)
-        if (soff[q] >= 0) cp_async16(dst + soff[q], uz + goff[q]);
+        if (soff[q] >= 0) cp_async16(dst + (unsigned)soff[q] * 4u, uz + goff[q]);
     }
     cp_async_commit();
   };
@@ -562,7 +580,7 @@ __global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, con
   const int jb = y0 + ty * RY;
   const int sbase = (R + ty * RY) * SX + XH + 4 * tx;
   const int nx = N - i;  // points of the thread's four inside the grid
-  const bool xedge = i < R || i + 3 >= N - R;
+  const bool xedge = i == 0 || nx <= 5;  // a[] holds a cell outside the domain
   int idx0 = z0 * plane + jb * g.px + i;
   int cs = R;
   int fs_ = 2 * R + D;
@@ -603,6 +621,22 @@ __global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, con
         a[2] = 0.f; a[3] = P0[o0 - 1]; a[8] = P0[o0 + 4]; a[9] = 0.f;
       }
       a[4] = c[0]; a[5] = c[1]; a[6] = c[2]; a[7] = c[3];
+      // x boundary rule on the ten x values (a[m] sits at x = i + m - 4): the
+      // cells -1 and N read 0, the ghosts -2 and N+1 minus u(0) and u(N-1)
+      if (xedge) {
+        if (i == 0) {
+          a[3] = 0.f;
+          a[2] = -a[4];
+        }
+        switch (nx) {
+          case 1: a[5] = 0.f; a[6] = R == 2 ? -a[4] : a[6]; break;
+          case 2: a[6] = 0.f; a[7] = R == 2 ? -a[5] : a[7]; break;
+          case 3: a[7] = 0.f; a[8] = R == 2 ? -a[6] : a[8]; break;
+          case 4: a[8] = 0.f; a[9] = R == 2 ? -a[7] : a[9]; break;
+          case 5: a[9] = 0.f; break;
+          default: break;
+        }
+      }
       const float4 ym1 = col[r + R - 1], yp1 = col[r + R + 1];
       const float4 zm1 = *reinterpret_cast<const float4*>(Pm1 + o0);
       const float4 zp1 = *reinterpret_cast<const float4*>(Pp1 + o0);
@@ -630,10 +664,6 @@ __global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, con
           xp2v[q] = a[6 + q];
         }
       }
-      if (xedge) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fix_axis<float, R>(i + q, N, c[q], xm1v[q], xp1v[q], xm2v[q], xp2v[q]);
-      }
       if (j < R || j >= N - R) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) fix_axis<float, R>(j, N, c[q], ym1v[q], yp1v[q], ym2v[q], yp2v[q]);
@@ -655,15 +685,10 @@ __global__ void __launch_bounds__(32 * TYT) k_tile4(Grid g, int nzc, int zc, con
   cp_async_wait<0>();
 }
 
-template <typename T, int ORDER, int TYT, int RY, int D>
-constexpr int tile4_smem_bytes() {
-  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) * (128 + 8) * 4;
-}
-
 template <int ORDER, int TYT, int RY, int D, typename Op>
 cudaError_t launch_tile4(const Grid& g, int B, int nzc, int zc, const int* active, const Op& op,
                          cudaStream_t st) {
-  constexpr int smem = tile4_smem_bytes<float, ORDER, TYT, RY, D>();
+  constexpr int smem = tile4_smem<ORDER, TYT, RY, D>();
   if (smem > 48 * 1024) {
     static bool set = false;
     if (!set) {
@@ -705,12 +730,18 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
     case 4: e = launch_tile<ORDER, 4, 4, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
     case 5: e = launch_tile<ORDER, 4, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
     case 6: e = launch_tile<ORDER, 8, 2, 6, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;
-    case 7: case 8: case 9: case 10:
+    case 7: case 8: case 9: case 10: case 11: case 12: case 13: case 14:
       if constexpr (has_vec4<Op>::value && !NORM) {
-        if (kind == 7) e = launch_tile4<ORDER, 4, 2, 3>(g, B, nzc, zc, active, op, st);
-        else if (kind == 8) e = launch_tile4<ORDER, 8, 1, 3>(g, B, nzc, zc, active, op, st);
-        else if (kind == 9) e = launch_tile4<ORDER, 4, 4, 3>(g, B, nzc, zc, active, op, st);
-        else e = launch_tile4<ORDER, 8, 2, 3>(g, B, nzc, zc, active, op, st);
+        switch (kind) {
+          case 7: e = launch_tile4<ORDER, 4, 2, 3>(g, B, nzc, zc, active, op, st); break;
+          case 8: e = launch_tile4<ORDER, 8, 1, 3>(g, B, nzc, zc, active, op, st); break;
+          case 9: e = launch_tile4<ORDER, 4, 4, 3>(g, B, nzc, zc, active, op, st); break;
+          case 10: e = launch_tile4<ORDER, 8, 2, 3>(g, B, nzc, zc, active, op, st); break;
+          case 11: e = launch_tile4<ORDER, 4, 2, 6>(g, B, nzc, zc, active, op, st); break;
+          case 12: e = launch_tile4<ORDER, 8, 1, 6>(g, B, nzc, zc, active, op, st); break;
+          case 13: e = launch_tile4<ORDER, 4, 2, 10>(g, B, nzc, zc, active, op, st); break;
+          default: e = launch_tile4<ORDER, 2, 2, 6>(g, B, nzc, zc, active, op, st); break;
+        }
         break;
       }
       [[fallthrough]];

@@ -295,7 +295,8 @@ def test_graphs_and_autotune_change_nothing(H, oracle, precision):
         assert rel(outs[1][0], ref) <= 1e-11
 
 
-SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (8, 2), (9, 16), (10, 64)]
+SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (8, 2), (9, 16), (10, 64),
+          (11, 16), (12, 4), (13, 32), (14, 8)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
