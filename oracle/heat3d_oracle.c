@@ -15,11 +15,15 @@
  * Readings of points the paper leaves open (all stated once more at the
  * function that uses them):
  *   - fine stencil: 4th-order "wide" 13-point Laplacian with odd-reflection
- *     ghosts u_{-1} = -u_1, u_{N+2} = -u_N (the paper's compact stencil is not
- *     built);
+ *     ghosts u_{-1} = -u_1, u_{N+2} = -u_N (order 4), or the 4th-order compact
+ *     19-point Mehrstellen operator (order 19, Sec. 1 and Sec. 1.2): the
+ *     semi-discrete system is W u' = nu L u + W f with the weighting matrix
+ *     W = I + (h^2/12) Delta_7; SDC runs in that weighted form and the FAS
+ *     restriction applies W^{-1} (by multigrid) to the fine integrals;
  *   - M counts Gauss-Lobatto nodes including both ends of the step;
  *   - multigrid: damped Jacobi (omega 6/7 for 7 points, 9/11 for 13 points,
- *     constant interior diagonal), full-weighting restriction, trilinear
+ *     12/11 for the compact operator, constant interior diagonal),
+ *     full-weighting restriction, trilinear
  *     prolongation, rediscretised coarse operators, N -> (N-1)/2 down to one
  *     unknown solved exactly (Sec. 1.2);
  *   - solve stop rule: max|b - A u| <= tol, checked before every cycle;
@@ -37,10 +41,13 @@
 #define OR_ENOTCONV (-3)
 
 #define OR_PI 3.14159265358979323846
+#define OR_COMPACT 19 /* order code of the compact 19-point stencil */
+/* The W-solve of the FAS restriction stops at max(mg_tol, OR_W_REL * |r|). */
+#define OR_W_REL 1e-2
 
 typedef struct {
   int N;     /* interior points per axis */
-  int order; /* 2: 7-point Laplacian, 4: 13-point wide Laplacian */
+  int order; /* 2: 7-point Laplacian, 4: 13-point wide Laplacian, 19: compact */
   int M;     /* Gauss-Lobatto nodes per step, both end points included */
 } or_level;
 
@@ -92,9 +99,46 @@ static double value_at(const double* u, int N, int i, int j, int k) {
   return s * u[id3(N, ii, jj, kk)];
 }
 
+/* Compact (Mehrstellen) Laplacian L u = (1/(6 h^2)) (-24 u + 2 * (sum of the
+ * 6 face neighbours) + (sum of the 12 edge neighbours)), zero boundary. */
+static void compact_laplacian(int N, const double* u, double* out) {
+  double h = 1.0 / (N + 1);
+  for (int k = 1; k <= N; ++k)
+    for (int j = 1; j <= N; ++j)
+      for (int i = 1; i <= N; ++i) {
+        double faces = 0.0, edges = 0.0;
+        for (int dk = -1; dk <= 1; ++dk)
+          for (int dj = -1; dj <= 1; ++dj)
+            for (int di = -1; di <= 1; ++di) {
+              int nz = (di != 0) + (dj != 0) + (dk != 0);
+              double v = value_at(u, N, i + di, j + dj, k + dk);
+              if (nz == 1) faces += v;
+              if (nz == 2) edges += v;
+            }
+        out[id3(N, i, j, k)] = (-24.0 * u[id3(N, i, j, k)] + 2.0 * faces + edges) / (6.0 * h * h);
+      }
+}
+
+/* out = W u: the weighting matrix of the compact scheme,
+ * (6 u + sum of the 6 face neighbours) / 12 = u + (h^2 / 12) Delta_7 u; the
+ * identity for the other stencils. */
+void or_weight(int N, int order, const double* u, double* out) {
+  if (order != OR_COMPACT) { memcpy(out, u, n3(N) * sizeof(double)); return; }
+  for (int k = 1; k <= N; ++k)
+    for (int j = 1; j <= N; ++j)
+      for (int i = 1; i <= N; ++i) {
+        double faces = value_at(u, N, i - 1, j, k) + value_at(u, N, i + 1, j, k) +
+                       value_at(u, N, i, j - 1, k) + value_at(u, N, i, j + 1, k) +
+                       value_at(u, N, i, j, k - 1) + value_at(u, N, i, j, k + 1);
+        out[id3(N, i, j, k)] = (6.0 * u[id3(N, i, j, k)] + faces) / 12.0;
+      }
+}
+
 /* out = Delta_h u.  order 2: (u_{-1} - 2 u + u_{+1}) / h^2 per axis;
- * order 4: (-u_{-2} + 16 u_{-1} - 30 u + 16 u_{+1} - u_{+2}) / (12 h^2). */
+ * order 4: (-u_{-2} + 16 u_{-1} - 30 u + 16 u_{+1} - u_{+2}) / (12 h^2);
+ * order 19: the compact operator L (W^{-1} L approximates Delta). */
 void or_laplacian(int N, int order, const double* u, double* out) {
+  if (order == OR_COMPACT) { compact_laplacian(N, u, out); return; }
   double h = 1.0 / (N + 1);
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j)
@@ -117,12 +161,16 @@ void or_laplacian(int N, int order, const double* u, double* out) {
       }
 }
 
-/* out = A u with A = I - c Delta_h: the matrix of one implicit-Euler
- * substep (Sec. 1.1, the sweep equation, implicit part). */
+/* out = A u with A = W - c Delta_h: the matrix of one implicit-Euler
+ * substep (Sec. 1.1, the sweep equation, implicit part); W = I except for
+ * the compact stencil. */
 void or_apply_A(int N, int order, double c, const double* u, double* out) {
-  or_laplacian(N, order, u, out);
   size_t n = n3(N);
-  for (size_t p = 0; p < n; ++p) out[p] = u[p] - c * out[p];
+  double* w = (double*)malloc(n * sizeof(double));
+  or_weight(N, order, u, w);
+  or_laplacian(N, order, u, out);
+  for (size_t p = 0; p < n; ++p) out[p] = w[p] - c * out[p];
+  free(w);
 }
 
 /* r = b - A u */
@@ -146,11 +194,18 @@ double or_maxabs(size_t n, const double* v) {
 /* coarsest grid of one unknown)                                             */
 /* ------------------------------------------------------------------------ */
 
-static double jacobi_omega(int order) { return order == 2 ? 6.0 / 7.0 : 9.0 / 11.0; }
+/* Damping factors from local Fourier analysis of each stencil's Laplacian:
+ * 2 / (smallest + largest high-frequency symbol of the Jacobi-normalised
+ * operator); the compact operator's range is [1/2, 4/3]. */
+static double jacobi_omega(int order) {
+  if (order == OR_COMPACT) return 12.0 / 11.0;
+  return order == 2 ? 6.0 / 7.0 : 9.0 / 11.0;
+}
 
 /* Diagonal used by the smoother: the constant interior diagonal of A. */
 static double jacobi_diag(int N, int order, double c) {
   double h = 1.0 / (N + 1);
+  if (order == OR_COMPACT) return 0.5 + c * 4.0 / (h * h);
   return order == 2 ? 1.0 + c * 6.0 / (h * h) : 1.0 + c * 90.0 / (12.0 * h * h);
 }
 
@@ -239,7 +294,7 @@ static int mg_levels_ok(int N) {
   return n == 1;
 }
 
-/* Solve (I - c Delta_h) u = b, warm-started from u.  tol >= 0: cycle while
+/* Solve (W - c Delta_h) u = b, warm-started from u.  tol >= 0: cycle while
  * max|b - A u| > tol, at most max_cycles; tol < 0: exactly max_cycles. */
 int or_mg_solve(int N, int order, double c, double* u, const double* b, double tol,
                 int max_cycles, int nu1, int nu2, int* cycles_out, double* res_out) {
@@ -380,7 +435,8 @@ double or_sdc_residual(const or_level* L, const or_problem* P, double t0, double
                        const double* U, const double* F, const double* tauQ);
 
 /* One IMEX-Euler SDC sweep over [t0, t0 + dt] (the sweep equation of
- * Sec. 1.1), U and F updated in place.  tauQ (M fields or NULL) is the FAS
+ * Sec. 1.1), U and F updated in place; for the compact stencil in the
+ * weighted form (W - dt_m nu L) U_{m+1} = W U_m - dt_m F_{m+1} + quadrature.  tauQ (M fields or NULL) is the FAS
  * correction in cumulative form; the sweep adds tauQ_{m+1} - tauQ_m on the
  * substep m.  The explicit part is the forcing, so its difference term is
  * evaluated as written and is zero. */
@@ -400,19 +456,24 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
   }
   double* Fold = (double*)malloc((size_t)M * n * sizeof(double));
   double* phi = (double*)malloc(n * sizeof(double));
+  double* wphi = (double*)malloc(n * sizeof(double));
+  double* wu = (double*)malloc(n * sizeof(double));
   double* rhs = (double*)malloc(n * sizeof(double));
   memcpy(Fold, F, (size_t)M * n * sizeof(double));
   or_phi(N, phi);
+  /* the weighted form W U' = F + W f (W = I but for the compact stencil) */
+  or_weight(N, L->order, phi, wphi);
   for (int m = 0; m + 1 < M; ++m) {
     double tm = t0 + dt * tau[m], tm1 = t0 + dt * tau[m + 1];
     double dtm = dt * (tau[m + 1] - tau[m]);
+    or_weight(N, L->order, U + m * n, wu);
     for (size_t p = 0; p < n; ++p) {
-      double fe_new = phi[p] * forcing_g(P, tm); /* f^E(U^{k+1}_m, t_m) */
-      double fe_old = phi[p] * forcing_g(P, tm); /* f^E(U^k_m, t_m) */
+      double fe_new = wphi[p] * forcing_g(P, tm); /* W f^E(U^{k+1}_m, t_m) */
+      double fe_old = wphi[p] * forcing_g(P, tm); /* W f^E(U^k_m, t_m) */
       double quad = 0.0;
       for (int j = 0; j < M; ++j)
-        quad += S[m * M + j] * (Fold[j * n + p] + phi[p] * forcing_g(P, t0 + dt * tau[j]));
-      double v = U[m * n + p] + dtm * (fe_new - fe_old) - dtm * Fold[(m + 1) * n + p] + dt * quad;
+        quad += S[m * M + j] * (Fold[j * n + p] + wphi[p] * forcing_g(P, t0 + dt * tau[j]));
+      double v = wu[p] + dtm * (fe_new - fe_old) - dtm * Fold[(m + 1) * n + p] + dt * quad;
       if (tauQ) v += tauQ[(m + 1) * n + p] - tauQ[m * n + p];
       rhs[p] = v;
     }
@@ -427,12 +488,13 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
     eval_fI(L, P, U + (m + 1) * n, F + (m + 1) * n);
   }
   if (st) st->sweeps += 1;
-  free(Fold); free(phi); free(rhs);
+  free(Fold); free(phi); free(wphi); free(wu); free(rhs);
   return status;
 }
 
-/* Collocation residual max_m max_x |U_0 + dt sum_j Q_{m,j} (F_j + f^E_j)
- * + tauQ_m - U_m| over the nodes m = 1..M-1. */
+/* Collocation residual max_m max_x |W U_0 + dt sum_j Q_{m,j} (F_j + W f^E_j)
+ * + tauQ_m - W U_m| over the nodes m = 1..M-1 (W = I but for the compact
+ * stencil, whose residual is taken in the weighted form). */
 double or_sdc_residual(const or_level* L, const or_problem* P, double t0, double dt,
                        const double* U, const double* F, const double* tauQ) {
   int N = L->N, M = L->M;
@@ -441,19 +503,23 @@ double or_sdc_residual(const or_level* L, const or_problem* P, double t0, double
   or_gl_nodes(M, tau);
   or_qmatrix(M, Q);
   double* phi = (double*)malloc(n * sizeof(double));
+  double* wphi = (double*)malloc(n * sizeof(double));
+  double* wu = (double*)malloc((size_t)M * n * sizeof(double));
   or_phi(N, phi);
+  or_weight(N, L->order, phi, wphi);
+  for (int m = 0; m < M; ++m) or_weight(N, L->order, U + m * n, wu + m * n);
   double res = 0.0;
   for (int m = 1; m < M; ++m)
     for (size_t p = 0; p < n; ++p) {
       double quad = 0.0;
       for (int j = 0; j < M; ++j)
-        quad += Q[m * M + j] * (F[j * n + p] + phi[p] * forcing_g(P, t0 + dt * tau[j]));
-      double v = U[p] + dt * quad - U[m * n + p];
+        quad += Q[m * M + j] * (F[j * n + p] + wphi[p] * forcing_g(P, t0 + dt * tau[j]));
+      double v = wu[p] + dt * quad - wu[m * n + p];
       if (tauQ) v += tauQ[m * n + p];
       double a = fabs(v);
       if (a > res || a != a) res = a;
     }
-  free(phi);
+  free(phi); free(wphi); free(wu);
   return res;
 }
 
@@ -507,6 +573,7 @@ static int node_map(int MF, int MG, int m) {
 
 static int fas_check(const or_level* F, const or_level* G) {
   if (!(F->N == G->N || F->N == 2 * G->N + 1)) return OR_EINVAL;
+  if (G->order == OR_COMPACT) return OR_EINVAL; /* compact: fine level only */
   double tf[8], tg[8];
   if (or_gl_nodes(F->M, tf) || or_gl_nodes(G->M, tg)) return OR_EINVAL;
   for (int m = 0; m < G->M; ++m)
@@ -526,11 +593,18 @@ static void inject(int NF, int NG, const double* uf, double* ug) {
  * in cumulative (Q) form:
  *   U^G_m = R U^F_{j(m)},  F^G_m = nu Delta^G U^G_m,
  *   tauQ_m = R(dt sum_j Q^F_{j(m),j} (F^F_j + f^E_j)) - dt sum_i Q^G_{m,i} (F^G_i + f^E_i).
+ * A compact fine level integrates the weighted system, so its integral is
+ * mapped back by W^{-1} before the injection (Sec. 1.2, the weighting-matrix
+ * inversion for the FAS correction), in the equivalent form
+ * U_j - U_0 + W^{-1} r: a multigrid solve of W x = r (c = 0), warm-started
+ * from r, to max|r - W x| <= max(mg_tol, OR_W_REL max|r|); node 0, whose
+ * integral is zero, is not solved.
  * UGr receives a copy of the restricted U^G for the later correction. */
-int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P, double t0,
-                    double dt, const double* UF, const double* FF, double* UG, double* FG,
-                    double* UGr, double* tauQ) {
+int or_fas_restrict_st(const or_level* LF, const or_level* LG, const or_problem* P, double t0,
+                       double dt, const double* UF, const double* FF, double* UG, double* FG,
+                       double* UGr, double* tauQ, or_stats* st) {
   if (fas_check(LF, LG) != OR_OK) return OR_EINVAL;
+  int status = OR_OK;
   int NF = LF->N, NG = LG->N, MF = LF->M, MG = LG->M;
   size_t nf = n3(NF), ng = n3(NG);
   double tf[8], tg[8], QF[64], QG[64];
@@ -538,8 +612,13 @@ int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P,
   double* phif = (double*)malloc(nf * sizeof(double));
   double* phig = (double*)malloc(ng * sizeof(double));
   double* tmpf = (double*)malloc(nf * sizeof(double));
+  double* xf = (double*)malloc(nf * sizeof(double));
   double* tmpg = (double*)malloc(ng * sizeof(double));
   or_phi(NF, phif); or_phi(NG, phig);
+  if (LF->order == OR_COMPACT) {
+    or_weight(NF, LF->order, phif, xf);
+    memcpy(phif, xf, nf * sizeof(double)); /* W f^E = g(t) W Phi on the fine level */
+  }
   for (int m = 0; m < MG; ++m) {
     int jm = node_map(MF, MG, m);
     inject(NF, NG, UF + (size_t)jm * nf, UG + (size_t)m * ng);
@@ -554,6 +633,29 @@ int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P,
         q += QF[jm * MF + j] * (FF[(size_t)j * nf + p] + phif[p] * forcing_g(P, t0 + dt * tf[j]));
       tmpf[p] = dt * q;
     }
+    if (LF->order == OR_COMPACT && jm != 0) {
+      /* W^{-1} (integral) = U_jm - U_0 + W^{-1} r with the weighted residual
+       * r = W U_0 + integral - W U_jm: only r goes through the solver, so an
+       * inexact solve changes the correction but not the fixed point. */
+      double* wu0 = (double*)malloc(nf * sizeof(double));
+      double* wuj = (double*)malloc(nf * sizeof(double));
+      or_weight(NF, LF->order, UF, wu0);
+      or_weight(NF, LF->order, UF + (size_t)jm * nf, wuj);
+      for (size_t p = 0; p < nf; ++p) tmpf[p] = wu0[p] + tmpf[p] - wuj[p];
+      double rmax = or_maxabs(nf, tmpf);
+      double wtol = P->mg_tol;
+      if (P->mg_tol >= 0 && OR_W_REL * rmax > wtol) wtol = OR_W_REL * rmax;
+      int cyc = 0;
+      double res = 0.0;
+      memcpy(xf, tmpf, nf * sizeof(double));
+      int rc = or_mg_solve(NF, LF->order, 0.0, xf, tmpf, wtol, P->mg_max, P->nu1, P->nu2,
+                           &cyc, &res);
+      if (rc == OR_ENOTCONV) { status = rc; if (st) st->notconv++; }
+      else if (rc != OR_OK) { status = rc; free(wu0); free(wuj); break; }
+      if (st) { st->vcycles += cyc; st->solves += 1; }
+      for (size_t p = 0; p < nf; ++p) tmpf[p] = UF[(size_t)jm * nf + p] - UF[p] + xf[p];
+      free(wu0); free(wuj);
+    }
     inject(NF, NG, tmpf, tmpg);
     for (size_t p = 0; p < ng; ++p) {
       double q = 0.0;
@@ -562,8 +664,14 @@ int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P,
       tauQ[(size_t)m * ng + p] = tmpg[p] - dt * q;
     }
   }
-  free(phif); free(phig); free(tmpf); free(tmpg);
-  return OR_OK;
+  free(phif); free(phig); free(tmpf); free(xf); free(tmpg);
+  return status;
+}
+
+int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P, double t0,
+                    double dt, const double* UF, const double* FF, double* UG, double* FG,
+                    double* UGr, double* tauQ) {
+  return or_fas_restrict_st(LF, LG, P, t0, dt, UF, FF, UG, FG, UGr, tauQ, NULL);
 }
 
 /* Coarse-to-fine correction: Delta_m = U^G_m - UGr_m at the coarse nodes,
@@ -641,7 +749,8 @@ int or_mlsdc_run(const or_level* LF, const or_level* LG, const or_problem* P, do
     double t0 = s * dt;
     or_spread(LF, P, ucur, UF, FF);
     if (o->predictor) {
-      or_fas_restrict(LF, LG, P, t0, dt, UF, FF, UG, FG, UGr, tQ);
+      if (or_fas_restrict_st(LF, LG, P, t0, dt, UF, FF, UG, FG, UGr, tQ, st) == OR_ENOTCONV)
+        status = OR_ENOTCONV;
       int rc = coarse_sweeps(LG, P, t0, dt, UG, FG, tQ, o->nsweeps_coarse, st);
       if (rc != OR_OK && rc != OR_ENOTCONV) { status = rc; goto done; }
       if (rc == OR_ENOTCONV) status = rc;
@@ -653,7 +762,8 @@ int or_mlsdc_run(const or_level* LF, const or_level* LG, const or_problem* P, do
         if (rc != OR_OK && rc != OR_ENOTCONV) { status = rc; goto done; }
         if (rc == OR_ENOTCONV) status = rc;
       }
-      or_fas_restrict(LF, LG, P, t0, dt, UF, FF, UG, FG, UGr, tQ);
+      if (or_fas_restrict_st(LF, LG, P, t0, dt, UF, FF, UG, FG, UGr, tQ, st) == OR_ENOTCONV)
+        status = OR_ENOTCONV;
       int rc = coarse_sweeps(LG, P, t0, dt, UG, FG, tQ, o->nsweeps_coarse, st);
       if (rc != OR_OK && rc != OR_ENOTCONV) { status = rc; goto done; }
       if (rc == OR_ENOTCONV) status = rc;
@@ -709,8 +819,9 @@ int or_pfasst_run(const or_level* LF, const or_level* LG, const or_problem* P, d
             if (rc == OR_ENOTCONV) status = rc;
           }
       for (int p = 0; p < PS; ++p)
-        or_fas_restrict(LF, LG, P, tb + p * dt, dt, UF + p * sf, FF + p * sf, UG + p * sg,
-                        FG + p * sg, UGr + p * sg, tQ + p * sg);
+        if (or_fas_restrict_st(LF, LG, P, tb + p * dt, dt, UF + p * sf, FF + p * sf, UG + p * sg,
+                               FG + p * sg, UGr + p * sg, tQ + p * sg, st) == OR_ENOTCONV)
+          status = OR_ENOTCONV;
       for (int p = 0; p < PS; ++p) {
         if (p > 0) {
           memcpy(UG + p * sg, UG + (p - 1) * sg + (size_t)(MG - 1) * ng, ng * sizeof(double));

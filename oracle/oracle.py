@@ -21,6 +21,7 @@ _SRC = os.path.join(_HERE, "heat3d_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_heat3d.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV = 0, -1, -2, -3
+COMPACT = 19  # order code of the compact (Mehrstellen) 19-point stencil
 
 
 def build(force: bool = False) -> str:
@@ -66,6 +67,7 @@ def lib():
         L = C.CDLL(build())
         P, I, D = C.POINTER, C.c_int, C.c_double
         L.or_laplacian.argtypes = [I, I, _dp, _dp]
+        L.or_weight.argtypes = [I, I, _dp, _dp]
         L.or_apply_A.argtypes = [I, I, D, _dp, _dp]
         L.or_residual.argtypes = [I, I, D, _dp, _dp, _dp]
         L.or_jacobi.argtypes = [I, I, D, _dp, _dp, _dp]
@@ -119,6 +121,14 @@ def laplacian(u, order):
     u = _c(u)
     out = np.empty_like(u)
     lib().or_laplacian(u.shape[0], order, u, out)
+    return out
+
+
+def weight(u, order):
+    """W u: the compact scheme's weighting matrix (the identity for orders 2 and 4)."""
+    u = _c(u)
+    out = np.empty_like(u)
+    lib().or_weight(u.shape[0], order, u, out)
     return out
 
 

@@ -46,6 +46,29 @@ def A_dense(N: int, order: int, c: float):
     return np.eye(N**3) - c * lap
 
 
+def compact_eigs(N: int, k):
+    """Eigenvalues of the compact scheme on sin(k1 pi x) sin(k2 pi y) sin(k3 pi z),
+    from its symbol with c_a = cos(k_a pi h): the 19-point operator gives
+    (-24 + 4 (c1 + c2 + c3) + 4 (c1 c2 + c1 c3 + c2 c3)) / (6 h^2) (faces weigh
+    2, edges 1), the weighting matrix (3 + c1 + c2 + c3) / 6.  Returns (lam_L, lam_W)."""
+    h = 1.0 / (N + 1)
+    c = [np.cos(np.asarray(ka, dtype=np.float64) * np.pi * h) for ka in k]
+    s1 = c[0] + c[1] + c[2]
+    s2 = c[0] * c[1] + c[0] * c[2] + c[1] * c[2]
+    return (-24.0 + 4.0 * s1 + 4.0 * s2) / (6.0 * h * h), (3.0 + s1) / 6.0
+
+
+def compact_A_dense(N: int, c: float):
+    """W - c L of the compact scheme as V diag(lam_W - c lam_L) V^T over the 3-D
+    sine basis (sines are its eigenvectors)."""
+    V1 = dst_basis(N)
+    V = np.kron(np.kron(V1, V1), V1)
+    k = np.arange(1, N + 1)
+    K3, K2, K1 = np.meshgrid(k, k, k, indexing="ij")  # z, y, x order of the vector
+    lamL, lamW = compact_eigs(N, (K1.reshape(-1), K2.reshape(-1), K3.reshape(-1)))
+    return V @ np.diag(lamW - c * lamL) @ V.T
+
+
 def gl_nodes_legendre(M: int):
     """Gauss-Lobatto nodes on [0,1]: ends plus roots of P'_{M-1} (numpy legendre)."""
     from numpy.polynomial import legendre as Lg

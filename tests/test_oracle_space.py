@@ -116,3 +116,86 @@ def test_full_weighting_properties(oracle):
     ref = t  # shape (Nf, Nf, Nf): interpolated from the padded coarse grid
     out = oracle.prolong_add(e, np.zeros((Nf, Nf, Nf)))
     assert np.abs(out - ref).max() <= 1e-14
+
+
+# --------------------------------------------------------------------------
+# compact (Mehrstellen) fine stencil: W u' = nu L u + W f (Sec. 1, Sec. 1.2)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N,k", [(7, (1, 1, 1)), (12, (2, 5, 3)), (1, (1, 1, 1)), (2, (2, 1, 2)),
+                                 (15, (15, 1, 8))])
+def test_compact_sine_eigenmodes(oracle, N, k):
+    """L and W multiply each sine mode by their symbols (faces 2, edges 1 for L;
+    centre 6, faces 1 for 12 W), exact to rounding; the mode (N, ..) checks the
+    boundary rows."""
+    u = inputs.sine_mode(N, *k)
+    lamL, lamW = ind.compact_eigs(N, k)
+    assert np.abs(oracle.laplacian(u, oracle.COMPACT) - lamL * u).max() <= 1e-12 * abs(lamL) * 10
+    assert np.abs(oracle.weight(u, oracle.COMPACT) - lamW * u).max() <= 1e-14
+
+
+def test_compact_is_fourth_order_consistent(oracle):
+    """W^{-1} L on the (1,1,1) mode approximates -3 pi^2 with error O(h^4)."""
+    errs = []
+    for N in (7, 15, 31):
+        lamL, lamW = ind.compact_eigs(N, (1, 1, 1))
+        errs.append(abs(lamL / lamW + 3 * np.pi**2))
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(np.abs(rates - 4.0) <= 0.1), rates
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5])
+def test_compact_operator_equals_spectral_matrix(oracle, N):
+    """(W - c L) u for random u equals the sine-basis matrix: every row,
+    including edges and corners of the cube."""
+    c = 0.37 / (N + 1) ** 2
+    A = ind.compact_A_dense(N, c)
+    u = inputs.random_field(N, seed=21 + N)
+    ref = (A @ u.reshape(-1)).reshape(u.shape)
+    out = oracle.apply_A(u, oracle.COMPACT, c)
+    assert np.abs(out - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,ch2", [(1, 3.0), (3, 3.0), (7, 3.0), (7, 0.2)])
+def test_compact_mg_matches_dense_solve(oracle, N, ch2):
+    """Multigrid on W - c L iterated to 1e-14 equals a dense solve."""
+    c = ch2 / (N + 1) ** 2
+    A = ind.compact_A_dense(N, c)
+    b = inputs.random_field(N, seed=6)
+    u, rc, cyc, res = oracle.mg_solve(np.zeros_like(b), b, oracle.COMPACT, c, tol=1e-14,
+                                      max_cycles=300)
+    assert rc == oracle.OK and res <= 1e-14
+    ref = np.linalg.solve(A, b.reshape(-1)).reshape(b.shape)
+    assert np.abs(u - ref).max() <= 1e-12 * max(1.0, np.abs(ref).max())
+
+
+def test_compact_weight_solve(oracle):
+    """The weighting-matrix inversion (multigrid with c = 0) on a smooth
+    right-hand side reaches the dense W^{-1} b."""
+    N = 15
+    b = inputs.smooth_random_field(N, seed=2, kmax=4)
+    u, rc, cyc, res = oracle.mg_solve(b.copy(), b, oracle.COMPACT, 0.0, tol=1e-13, max_cycles=200)
+    assert rc == oracle.OK
+    x = np.zeros_like(b)
+    for kz in range(1, 5):
+        for ky in range(1, 5):
+            for kx in range(1, 5):
+                m = inputs.sine_mode(N, kx, ky, kz)
+                coef = np.sum(b * m) / np.sum(m * m)
+                x += coef / ind.compact_eigs(N, (kx, ky, kz))[1] * m
+    assert np.abs(u - x).max() <= 1e-11
+
+
+@pytest.mark.parametrize("N,ch2", [(15, 20.0), (31, 20.0), (31, 1.0)])
+def test_compact_mg_contraction(oracle, N, ch2):
+    """V(2,1) with omega = 12/11 contracts the compact system's residual by
+    at least 0.5 per cycle (diffusion-dominated and balanced c h^-2)."""
+    c = ch2 / (N + 1) ** 2
+    b = inputs.random_field(N, seed=3)
+    u = np.zeros_like(b)
+    prev = np.abs(oracle.residual(u, b, oracle.COMPACT, c)).max()
+    for _ in range(5):
+        u = oracle.vcycle(u, b, oracle.COMPACT, c)
+        r = np.abs(oracle.residual(u, b, oracle.COMPACT, c)).max()
+        assert r <= 0.5 * prev
+        prev = r

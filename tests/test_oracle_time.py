@@ -247,3 +247,73 @@ def test_fas_interpolation_reproduces_quadratic_in_time(oracle):
     for j in (0, 3):
         ref = ((lam_op - np.eye(15**3)) @ UF2[j].reshape(-1)).reshape(UF2[j].shape)
         assert np.abs(FF2[j] - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+# --------------------------------------------------------------------------
+# compact fine stencil: SDC in the weighted form, W^{-1} in the FAS restriction
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M,k", [(3, (1, 1, 1)), (5, (1, 1, 1)), (5, (2, 1, 3))])
+def test_compact_sdc_converges_to_collocation_of_mode(oracle, M, k):
+    """On one sine mode the weighted system W a' Phi = nu L a Phi + g W Phi is
+    the scalar ODE a' = nu (lam_L / lam_W) a + g: SDC iterated to convergence
+    equals its collocation solution, and the weighted residual vanishes."""
+    N, dt, t0 = 7, 0.125, 0.25
+    prob = oracle.Prob(**PROB_TIGHT)
+    if k != (1, 1, 1):
+        prob.forcing = 0
+    u0 = inputs.sine_mode(N, *k)
+    U, F = oracle.spread(N, oracle.COMPACT, M, prob, u0)
+    for _ in range(40):
+        U, F, rc, st = oracle.sdc_sweep(N, oracle.COMPACT, M, prob, t0, dt, U, F)
+        assert rc == oracle.OK
+    lamL, lamW = ind.compact_eigs(N, k)
+    a = ind.scalar_collocation(0.1 * lamL / lamW, 1.0, t0, dt, 0.1, 1.0,
+                               forcing=prob.forcing == 1)(M)
+    assert max(np.abs(U[m] - a[m] * u0).max() for m in range(M)) <= 1e-12
+    assert oracle.sdc_residual(N, oracle.COMPACT, M, prob, t0, dt, U, F) <= 1e-12
+
+
+def test_compact_spatial_order_against_analytic(oracle):
+    """Converged 5-node collocation on the compact stencil: the error against
+    u = Phi cos t (exact forcing kappa = 3) falls like h^4."""
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=3.0, mg_tol=1e-13, mg_max=100)
+    errs = []
+    for N in (3, 7, 15):
+        u0 = inputs.sine_mode(N)
+        uT, rc, _ = oracle.sdc_run(N, oracle.COMPACT, 5, prob, 0.125, 1, 12, u0, tol=1e-13)
+        errs.append(np.abs(uT - np.cos(0.125) * u0).max())
+    rate = np.log2(errs[1] / errs[2])
+    assert abs(rate - 4.0) <= 0.3, errs
+
+
+def test_compact_fas_leaves_fine_collocation_solution_fixed(oracle):
+    """A compact fine level holding its (weighted) collocation solution is a
+    fixed point of restrict + FAS-corrected coarse sweep + interpolate; this
+    needs the W^{-1} of the fine integrals in tau."""
+    fine, coarse = (15, oracle.COMPACT, 5), (7, 2, 3)
+    prob = oracle.Prob(**PROB_TIGHT)
+    dt, t0 = 1.0 / 16, 0.5
+    u0 = inputs.smooth_random_field(15, seed=4, kmax=4)
+    U, F = oracle.spread(*fine, prob, u0)
+    for _ in range(30):
+        U, F, rc, _ = oracle.sdc_sweep(*fine, prob, t0, dt, U, F)
+    assert oracle.sdc_residual(*fine, prob, t0, dt, U, F) <= 1e-12
+    UG, FG, UGr, tQ = oracle.fas_restrict(fine, coarse, prob, t0, dt, U, F)
+    assert oracle.sdc_residual(*coarse, prob, t0, dt, UG, FG, tQ) <= 1e-11
+    UG2, FG2, rc, _ = oracle.sdc_sweep(*coarse, prob, t0, dt, UG, FG, tQ)
+    assert np.abs(UG2 - UGr).max() <= 1e-11
+    U2, F2 = oracle.fas_interpolate(fine, coarse, prob, UG2, UGr, U)
+    assert np.abs(U2 - U).max() <= 1e-11
+
+
+def test_compact_mlsdc_converges_to_sdc_collocation(oracle):
+    """MLSDC with a compact fine level (7-point coarse level) and compact SDC
+    reach the same collocation solution."""
+    fine, coarse = (15, oracle.COMPACT, 5), (7, 2, 3)
+    prob = oracle.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    u0 = inputs.sine_mode(15)
+    a, rc, st = oracle.mlsdc_run(fine, coarse, prob, 1 / 16, 2, u0, max_iters=60, tol=1e-12)
+    b, rc2, _ = oracle.sdc_run(*fine, prob, 1 / 16, 2, 60, u0, tol=1e-12)
+    assert rc == oracle.OK and rc2 == oracle.OK
+    assert np.abs(a - b).max() <= 1e-10
