@@ -51,11 +51,20 @@ extern "C" {
 
 #define HEAT3D_MAX_NODES 5
 
+/* Stencil code (heat3d_level.order) of the fourth-order compact 19-point
+ * (Mehrstellen) discretisation, the paper's fine-level stencil (Sec. 1):
+ * W u' = nu L u + W f with L = (1/(6h^2)) (-24 u + 2 * faces + edges) and the
+ * weighting matrix W = (6 u + faces) / 12.  SDC runs in this weighted form
+ * (its collocation residual is the weighted one) and the FAS restriction
+ * applies W^{-1} by multigrid (Sec. 1.2).  Fine level only. */
+#define HEAT3D_COMPACT 19
+
 /* One level of the space-time hierarchy (Sec. 1: PFASST coarsens nodes, mesh
  * and stencil order). */
 typedef struct {
   int N;     /* interior points per axis; must be 2^k - 1 (multigrid halving), <= 1023 */
-  int order; /* 2: 7-point Laplacian; 4: 13-point wide Laplacian (odd-reflection ghosts) */
+  int order; /* 2: 7-point Laplacian; 4: 13-point wide Laplacian (odd-reflection ghosts);
+                HEAT3D_COMPACT: 19-point compact stencil (level 0 only) */
   int M;     /* Gauss-Lobatto nodes per step, both ends included, 2..5 */
 } heat3d_level;
 
@@ -141,10 +150,12 @@ const char* heat3d_last_error(const heat3d_ctx* ctx);
 int heat3d_set_stream(heat3d_ctx* ctx, void* stream);
 
 /* out = nu * Delta_h u on level `level`'s grid (Sec. 1 method of lines;
- * 7-point or wide stencil).  u, out: device, dense N^3 FP64. */
+ * 7-point or wide stencil; nu L u, without W^{-1}, for the compact stencil).
+ * u, out: device, dense N^3 FP64. */
 int heat3d_apply_laplacian(heat3d_ctx* ctx, int level, const double* u, double* out);
 
-/* Solves (I - c Delta_h) u = rhs by V(nu1, nu2) multigrid cycles in the
+/* Solves (I - c Delta_h) u = rhs ((W - c L) u = rhs for the compact
+ * stencil) by V(nu1, nu2) multigrid cycles in the
  * context's precision (Sec. 1.2; coarsening to one unknown).  u is the warm
  * start and the result.  max_cycles/tol as in heat3d_mg.  rhs, u: device,
  * dense N^3 FP64.  Returns HEAT3D_ENOTCONV when tol >= 0 is not reached. */

@@ -32,14 +32,19 @@ inline Grid make_grid(int N) {
   return g;
 }
 
-// Coefficients of A = I - c Delta_h on one multigrid level for one item:
+// Coefficients of A = W - c Delta_h on one multigrid level for one item:
 //   A u = d u - e S, with S = sum of the 6 nearest neighbours (7 points) or
-//   16 * (6 nearest) - (6 second neighbours) (wide stencil);
+//   16 * (6 nearest) - (6 second neighbours) (wide stencil), W = I;
+//   compact stencil: A u = d u - e S1 - e2 S2 with S1 the 6 face and S2 the
+//   12 edge neighbours (W - c L of the Mehrstellen scheme);
 //   wd = omega / d for damped Jacobi; a11 = A on the one-unknown grid.
 template <typename T>
 struct Coef {
-  T d, e, wd, a11;
+  T d, e, wd, a11, e2;
 };
+
+// Order code of the compact 19-point (Mehrstellen) stencil.
+constexpr int kCompact = 19;
 
 // Per item, per SDC level: step data of the sweep (Sec. 1.1).
 struct ItemSDC {

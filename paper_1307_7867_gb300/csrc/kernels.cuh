@@ -27,13 +27,16 @@ struct Shape {
 void count_launch();
 
 // ---- spatial operator (Sec. 1, method of lines) ----
-// out = alpha_b * L u with L = (S1 - 6u) (order 2) or (16 S1 - S2 - 90u)
-// (order 4); alpha_b = nu_b / h^2 or nu_b / (12 h^2).  When add_src != nullptr
-// also writes add_dst = u + add_src (the next substep's right-hand side).
+// out = alpha_b * L u with L = (S1 - 6u) (order 2), (16 S1 - S2 - 90u)
+// (order 4) or (2 S1 + S2 - 24 u) with S1 faces and S2 edges (compact, order
+// kCompact); alpha_b = nu_b / h^2, nu_b / (12 h^2) or nu_b / (6 h^2).  When
+// add_src != nullptr also writes add_dst = W u + add_src (the next substep's
+// right-hand side; W = I but for the compact stencil, whose W u is also
+// written to wu_out when given, at the stride of u).
 cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long long u_stride,
                        double* out, long long out_stride, const double* alpha,
                        const double* add_src, double* add_dst, long long add_stride,
-                       const int* active, Shape sh, cudaStream_t st);
+                       const int* active, Shape sh, cudaStream_t st, double* wu_out = nullptr);
 
 // ---- multigrid pieces (Sec. 1.2) ----
 // r = b - A u (FP64), written as TR into r_out; e0_out = wd * r (optional);
@@ -118,10 +121,20 @@ cudaError_t launch_integrals(int M, const Grid& g, int B, const double* U, const
 // ---- FAS (Sec. 1.1) ----
 // Injection of the fine nodes onto the coarse level and the fine Q-integral:
 //   UG_m = UGr_m = R UF_{jm},  qF_m = R(sum_j dtQ^F[jm][j] F^F_j) + gQ^F[jm] Phi
+// Compact fine level: X (field m-1 of each item at stride xs, for coarse node
+// m >= 1) holds W^{-1} r, and qF_m = R(U_jm - U_0 + X_{m-1}) instead.
 cudaError_t launch_fas_inject(int MF, int MG, const Grid& gf, const Grid& gg, int B,
                               const double* UF, const double* FF, double* UG, double* UGr,
                               double* qF, const ItemSDC* itF, const FasMap* map,
-                              const double* phig1d, cudaStream_t st);
+                              const double* phig1d, cudaStream_t st, const double* X = nullptr,
+                              long long xs = 0);
+// Compact fine level, fine node jm: weighted residual
+// r = W U_0 + sum_p dtQ[jm][p] F_p + gQ[jm] Phi - W U_jm into R (one field per
+// item) and X (item stride xs); max |r| per item into res_bits (zeroed by the caller).
+cudaError_t launch_fas_wresid(int MF, const Grid& gf, int B, int jm, const double* WU,
+                              const double* FF, const ItemSDC* itF, const double* phif1d,
+                              double* R, double* X, long long xs, unsigned long long* res_bits,
+                              cudaStream_t st);
 // tauQ_m = qF_m - sum_i dtQ^G[m][i] F^G_i - gQ^G[m] Phi;  tauS_m = tauQ_{m+1} - tauQ_m
 cudaError_t launch_fas_tau(int MG, const Grid& gg, int B, const double* qF, const double* FG,
                            double* tauS, const ItemSDC* itG, const double* phig1d,

@@ -178,7 +178,10 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
     const heat3d_level& L = cfg->levels[l];
     if (!is_pow2m1(L.N) || L.N > (1 << 10) - 1)
       return h3d_fail(c, HEAT3D_EINVAL, "level %d: N=%d must be 2^k-1 (<= 1023)", l, L.N);
-    if (L.order != 2 && L.order != 4) return h3d_fail(c, HEAT3D_EINVAL, "level %d: order must be 2 or 4", l);
+    if (L.order != 2 && L.order != 4 && L.order != kCompact)
+      return h3d_fail(c, HEAT3D_EINVAL, "level %d: order must be 2, 4 or HEAT3D_COMPACT", l);
+    if (l == 1 && L.order == kCompact)
+      return h3d_fail(c, HEAT3D_EINVAL, "the compact stencil is for the fine level only");
     if (L.M < 2 || L.M > kMaxNodes) return h3d_fail(c, HEAT3D_EINVAL, "level %d: M must be 2..5", l);
   }
   if (cfg->nlevels == 2) {
@@ -262,6 +265,10 @@ static size_t plan(heat3d_ctx* c, char* base) {
     L.U = (double*)take(fs * B * M);
     L.F = (double*)take(fs * B * M);
     L.I = (double*)take(fs * B * (M - 1));
+    if (L.L.order == kCompact) {
+      L.WU = (double*)take(fs * B * M);
+      L.Wr = (double*)take(fs * B);
+    }
     if (l == 1) {
       L.tauS = (double*)take(fs * B * (M - 1));
       L.UGr = (double*)take(fs * B * M);
@@ -282,7 +289,7 @@ static size_t plan(heat3d_ctx* c, char* base) {
     L.alpha_items = (double*)take(sizeof(double) * B);
     L.alpha_nodes = (double*)take(sizeof(double) * B * M);
     L.items_d = (ItemSDC*)take(sizeof(ItemSDC) * B);
-    L.nslots = M;  // M-1 substeps + one slot for mg_vcycle calls
+    L.nslots = M + 1;  // M-1 substeps, one slot for mg_vcycle calls, one for the W-solve
     L.coefT = take((ts == 8 ? sizeof(Coef<double>) : sizeof(Coef<float>)) * L.nslots * L.nmg * B);
     L.coef64 = (Coef<double>*)take(sizeof(Coef<double>) * L.nslots * B);
     L.norms = (unsigned long long*)take(sizeof(unsigned long long) * B);
@@ -300,10 +307,13 @@ void h3d_fill_item(heat3d_ctx* c, int lev, int item, double t0) {
   const double dt = L.dt[item], nu = L.nu[item];
   const bool forced = c->cfg.forcing != HEAT3D_FORCING_NONE;
   const double kap = kappa_of(c->cfg.forcing);
+  // compact stencil: the weighted system carries W f = g(t) W Phi, and Phi is
+  // an eigenvector of W with eigenvalue (3 + 3 cos(pi h)) / 6
+  const double wphi = L.L.order == kCompact ? (3.0 + 3.0 * cos(M_PI * L.h[0])) / 6.0 : 1.0;
   double g[kMaxNodes];
   for (int j = 0; j < M; ++j) {
     double t = t0 + dt * L.tau[j];
-    g[j] = forced ? -(sin(t) - kap * nu * M_PI * M_PI * cos(t)) : 0.0;
+    g[j] = forced ? -(sin(t) - kap * nu * M_PI * M_PI * cos(t)) * wphi : 0.0;
   }
   ItemSDC& it = L.items_h[item];
   memset(&it, 0, sizeof(it));
@@ -335,7 +345,8 @@ int h3d_upload_items(heat3d_ctx* c, int lev, int b0, int B) {
   return HEAT3D_OK;
 }
 
-// Multigrid coefficients of A = I - c Delta_h on every level, for slot `slot`
+// Multigrid coefficients of A = W - c Delta_h on every level (W = I but for
+// the compact stencil), for slot `slot`
 // of items [b0, b0 + B) with per-item c values.
 int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* cvals) {
   SdcLevel& L = c->lv[lev];
@@ -348,7 +359,16 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
     for (int b = 0; b < B; ++b) {
       const double cc = cvals[b];
       Coef<double> q;
-      if (order == 2) {
+      q.e2 = 0.0;
+      if (order == kCompact) {
+        // W - c L: centre 1/2 + 4c/h^2, faces 1/12 - c/(3h^2), edges -c/(6h^2);
+        // omega = 12/11 from local Fourier analysis of the Mehrstellen operator
+        q.e = cc / (3.0 * h * h) - 1.0 / 12.0;
+        q.e2 = cc / (6.0 * h * h);
+        q.d = 0.5 + 4.0 * cc / (h * h);
+        q.wd = (12.0 / 11.0) / q.d;
+        q.a11 = q.d;
+      } else if (order == 2) {
         q.e = cc / (h * h);
         q.d = 1.0 + 6.0 * q.e;
         q.wd = (6.0 / 7.0) / q.d;
@@ -371,7 +391,7 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
       std::vector<Coef<float>> cf(B);
       for (int b = 0; b < B; ++b) {
         const Coef<double>& q = cd[(size_t)k * B + b];
-        cf[b] = Coef<float>{(float)q.d, (float)q.e, (float)q.wd, (float)q.a11};
+        cf[b] = Coef<float>{(float)q.d, (float)q.e, (float)q.wd, (float)q.a11, (float)q.e2};
       }
       CK(cudaMemcpyAsync((Coef<float>*)L.coefT + base, cf.data(), sizeof(Coef<float>) * B,
                          cudaMemcpyHostToDevice, c->st));
@@ -393,11 +413,15 @@ int h3d_set_item_operators(heat3d_ctx* c, int lev, int b0, int B) {
     for (int b = 0; b < B; ++b) cv[b] = L.dt[b0 + b] * (L.tau[m + 1] - L.tau[m]) * L.nu[b0 + b];
     RET(h3d_set_coefs(c, lev, m, b0, B, cv.data()));
   }
+  if (L.L.order == kCompact) {  // the weighting matrix W = A at c = 0
+    for (int b = 0; b < B; ++b) cv[b] = 0.0;
+    RET(h3d_set_coefs(c, lev, M, b0, B, cv.data()));
+  }
   const double h = L.h[0];
   std::vector<double> ai(B), an((size_t)B * M);
   for (int b = 0; b < B; ++b) {
     double nu = L.nu[b0 + b];
-    ai[b] = L.L.order == 2 ? nu / (h * h) : nu / (12.0 * h * h);
+    ai[b] = L.L.order == 2 ? nu / (h * h) : L.L.order == 4 ? nu / (12.0 * h * h) : nu / (6.0 * h * h);
     for (int m = 0; m < M; ++m) an[(size_t)b * M + m] = ai[b];
   }
   CK(cudaMemcpyAsync(L.alpha_items + b0, ai.data(), sizeof(double) * B, cudaMemcpyHostToDevice, c->st));
@@ -430,8 +454,9 @@ static const Coef<T>* coefT(SdcLevel& L, int slot, int k, int b0) {
 template <typename T>
 static void jacobi_cost(int order, bool upd, double* bytes, double* dp, double* fl) {
   const double ts = sizeof(T);
-  const double ops = order == 2 ? 8.0 : 14.0;     // neighbour sums + 3 fused multiply-adds
-  const double flops = order == 2 ? 11.0 : 18.0;  // an FMA counts 2
+  // neighbour sums + fused multiply-adds (an FMA counts 2 flops)
+  const double ops = order == 2 ? 8.0 : order == 4 ? 14.0 : 20.0;
+  const double flops = order == 2 ? 11.0 : order == 4 ? 18.0 : 24.0;
   *bytes = upd ? 2.0 * ts + 16.0 : 3.0 * ts;
   *dp = (sizeof(T) == 8 ? ops : 0.0) + (upd ? 1.0 : 0.0);
   *fl = flops + (upd ? 1.0 : 0.0);
@@ -454,7 +479,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   T* t = mgbuf<T>(L, k, 2, b0);
   const Coef<T>* cf = coefT<T>(L, slot, k, b0);
   const size_t ts = sizeof(T), pts = (size_t)g.N * g.N * g.N * B;
-  if (k > 0 && c->cfg.fuse_coarse && g.N <= kFusedMaxN) {
+  if (k > 0 && c->cfg.fuse_coarse && g.N <= kFusedMaxN && L.L.order != kCompact) {
     // this level and every coarser one in a single kernel (same arithmetic)
     int Ns[kMaxLevels];
     const Coef<T>* cfs[kMaxLevels];
@@ -657,8 +682,8 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, L.shape64, st));
     if (pr >= 0) {
       // neighbour sums + 2 FMAs (+ the FP64 e0 multiply when T is double)
-      double dp = (order == 2 ? 7.0 : 13.0) + (sizeof(T) == 8 ? 1.0 : 0.0);
-      double fl = (order == 2 ? 9.0 : 16.0) + 1.0;
+      double dp = (order == 2 ? 7.0 : order == 4 ? 13.0 : 19.0) + (sizeof(T) == 8 ? 1.0 : 0.0);
+      double fl = (order == 2 ? 9.0 : order == 4 ? 16.0 : 22.0) + 1.0;
       h3d_prof_end(c, pr, (16.0 + 2.0 * sizeof(T)) * pts, dp * pts, fl * pts);
     }
     c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
@@ -752,13 +777,24 @@ int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, lon
 // SDC (Sec. 1.1)
 // ---------------------------------------------------------------------------
 
+// W U at the node fields of U (compact stencil only, else nullptr): WU has
+// the layout of U.
+static double* wu_of(SdcLevel& L, const double* u) {
+  return L.WU ? L.WU + (u - L.U) : nullptr;
+}
+
+// The fields the quadrature kernel takes as "U": W U for the compact stencil
+// (weighted collocation form), else U.
+static double* ubase_of(SdcLevel& L, double* u) { return L.WU ? L.WU + (u - L.U) : u; }
+
 // F at every node of items [b0, b0+B) from U.
 int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B) {
   SdcLevel& L = c->lv[lev];
   const int M = L.L.M;
   const long long fs = L.g.fs;
   CK(launch_lap(L.L.order, L.g, B * M, L.U + (size_t)b0 * M * fs, fs, L.F + (size_t)b0 * M * fs, fs,
-                L.alpha_nodes + (size_t)b0 * M, nullptr, nullptr, 0, nullptr, c->lv[lev].shape64, c->st));
+                L.alpha_nodes + (size_t)b0 * M, nullptr, nullptr, 0, nullptr, c->lv[lev].shape64, c->st,
+                wu_of(L, L.U + (size_t)b0 * M * fs)));
   c->bytes += 16.0 * L.L.N * L.L.N * (double)L.L.N * B * M;
   return HEAT3D_OK;
 }
@@ -770,7 +806,7 @@ int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector
   const int M = L.L.M;
   const long long fs = L.g.fs;
   CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, c->st));
-  CK(launch_integrals(M, L.g, B, L.U + (size_t)b0 * M * fs, L.F + (size_t)b0 * M * fs,
+  CK(launch_integrals(M, L.g, B, ubase_of(L, L.U + (size_t)b0 * M * fs), L.F + (size_t)b0 * M * fs,
                       (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
                       nullptr, L.items_d + b0, L.phi, L.norms + b0, nullptr, c->st));
   std::vector<double> n;
@@ -803,7 +839,8 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
   const bool adapt = mg.rel > 0 && mg.tol >= 0;
   const bool want = check_tol >= 0 || adapt;
   if (want) CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
-  CK(launch_integrals(M, L.g, B, U, F, (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
+  CK(launch_integrals(M, L.g, B, ubase_of(L, U), F,
+                      (lev == 1 && L.has_tau) ? L.tauS + (size_t)b0 * (M - 1) * fs : nullptr,
                       I, L.items_d + b0, L.phi, want ? L.norms + b0 : nullptr, nullptr, st));
   c->bytes += 8.0 * pts * (2 * M + (M - 1) + ((lev == 1 && L.has_tau) ? (M - 1) : 0));
   std::vector<double> tolv;
@@ -833,7 +870,7 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
     CK(launch_lap(L.L.order, L.g, B, U + (size_t)(m + 1) * fs, (long long)M * fs,
                   F + (size_t)(m + 1) * fs, (long long)M * fs, L.alpha_items + b0,
                   add ? I + (size_t)(m + 1) * fs : nullptr, add ? I + (size_t)(m + 1) * fs : nullptr,
-                  (long long)(M - 1) * fs, nullptr, L.shape64, st));
+                  (long long)(M - 1) * fs, nullptr, L.shape64, st, wu_of(L, U + (size_t)(m + 1) * fs)));
     c->bytes += pts * (16.0 + (add ? 16.0 : 0.0));
   }
   if (s) s->sweeps += 1;
@@ -844,14 +881,53 @@ int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_st
 // FAS between level 0 (fine) and level 1 (coarse)
 // ---------------------------------------------------------------------------
 
-int h3d_fas_restrict(heat3d_ctx* c, int b0, int B) {
+// Compact fine level: the fine integrals of the weighted system are mapped
+// back by W^{-1} (Sec. 1.2) in the form U_jm - U_0 + W^{-1} r, r the weighted
+// residual at node jm; the W-solve (multigrid slot M, c = 0) writes its
+// result into the fine integral fields I (free between sweeps) and stops at
+// max(mg.tol, 0.01 max|r_b|) per item.
+static int compact_wsolves(heat3d_ctx* c, int b0, int B, heat3d_stats* s) {
+  SdcLevel& F = c->lv[0];
+  const int MF = F.L.M, MG = c->lv[1].L.M;
+  const long long ff = F.g.fs;
+  const long long xs = (long long)(MF - 1) * ff;
+  const heat3d_mg& mg = c->cfg.mg;
+  int status = HEAT3D_OK;
+  std::vector<double> n, tolv(B);
+  for (int m = 1; m < MG; ++m) {
+    const int jm = c->map.jm[m];
+    double* X = F.I + (size_t)b0 * (MF - 1) * ff + (size_t)(m - 1) * ff;
+    double* R = F.Wr + (size_t)b0 * ff;
+    CK(cudaMemsetAsync(F.norms + b0, 0, sizeof(unsigned long long) * B, c->st));
+    CK(launch_fas_wresid(MF, F.g, B, jm, F.WU + (size_t)b0 * MF * ff, F.F + (size_t)b0 * MF * ff,
+                         F.items_d + b0, F.phi, R, X, xs, F.norms + b0, c->st));
+    c->bytes += 8.0 * F.L.N * F.L.N * (double)F.L.N * B * (MF + 4);
+    RET(read_norms(c, F, b0, B, n));
+    for (int b = 0; b < B; ++b) tolv[b] = std::max(mg.tol, 0.01 * n[b]);
+    int rc = h3d_mg_solve(c, 0, MF, b0, B, X, xs, R, ff, mg.max_cycles, mg.tol, s,
+                          mg.tol >= 0 ? tolv.data() : nullptr);
+    if (rc == HEAT3D_ENOTCONV) status = rc;
+    else if (rc < 0) return rc;
+  }
+  return status;
+}
+
+int h3d_fas_restrict(heat3d_ctx* c, int b0, int B, heat3d_stats* s) {
   SdcLevel &F = c->lv[0], &G = c->lv[1];
   const int MF = F.L.M, MG = G.L.M;
   const long long ff = F.g.fs, gf = G.g.fs;
   cudaStream_t st = c->st;
+  int status = HEAT3D_OK;
+  const double* X = nullptr;
+  if (F.L.order == kCompact) {
+    status = compact_wsolves(c, b0, B, s);
+    if (status < 0 && status != HEAT3D_ENOTCONV) return status;
+    X = F.I + (size_t)b0 * (MF - 1) * ff;
+  }
   CK(launch_fas_inject(MF, MG, F.g, G.g, B, F.U + (size_t)b0 * MF * ff, F.F + (size_t)b0 * MF * ff,
                        G.U + (size_t)b0 * MG * gf, G.UGr + (size_t)b0 * MG * gf,
-                       G.qF + (size_t)b0 * MG * gf, F.items_d + b0, c->map_d, F.phi, st));
+                       G.qF + (size_t)b0 * MG * gf, F.items_d + b0, c->map_d, F.phi, st, X,
+                       (long long)(MF - 1) * ff));
   CK(launch_lap(G.L.order, G.g, B * MG, G.U + (size_t)b0 * MG * gf, gf, G.F + (size_t)b0 * MG * gf, gf,
                 G.alpha_nodes + (size_t)b0 * MG, nullptr, nullptr, 0, nullptr, G.shape64, st));
   CK(launch_fas_tau(MG, G.g, B, G.qF + (size_t)b0 * MG * gf, G.F + (size_t)b0 * MG * gf,
@@ -859,7 +935,7 @@ int h3d_fas_restrict(heat3d_ctx* c, int b0, int B) {
   G.has_tau = true;
   const double pg = (double)G.L.N * G.L.N * G.L.N * B;
   c->bytes += pg * 8.0 * (2 * MF + 3 * MG) + pg * 16.0 * MG + pg * 8.0 * (2 * MG + MG - 1);
-  return HEAT3D_OK;
+  return status;
 }
 
 int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
@@ -927,7 +1003,8 @@ static int forward_fine(heat3d_ctx* c, int P) {
   CK(launch_copy(F.g, P - 1, F.U + (size_t)(MF - 1) * ff, (long long)MF * ff, F.U + (size_t)MF * ff,
                  (long long)MF * ff, c->st));
   CK(launch_lap(F.L.order, F.g, P - 1, F.U + (size_t)MF * ff, (long long)MF * ff, F.F + (size_t)MF * ff,
-                (long long)MF * ff, F.alpha_items + 1, nullptr, nullptr, 0, nullptr, F.shape64, c->st));
+                (long long)MF * ff, F.alpha_items + 1, nullptr, nullptr, 0, nullptr, F.shape64, c->st,
+                wu_of(F, F.U + (size_t)MF * ff)));
   return HEAT3D_OK;
 }
 
@@ -967,7 +1044,9 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
     } else {
       c->lv[1].has_tau = false;
       if (cfg.predictor) {
-        RET(h3d_fas_restrict(c, 0, P));
+        int rr = h3d_fas_restrict(c, 0, P, s);
+        if (rr == HEAT3D_ENOTCONV) status = rr;
+        else if (rr < 0) return rr;
         int rc = coarse_pass(c, P, s);
         if (rc == HEAT3D_ENOTCONV) status = rc;
         else if (rc < 0) return rc;
@@ -984,7 +1063,9 @@ int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s) {
           else if (rc < 0) return rc;
         }
         if (done) break;
-        RET(h3d_fas_restrict(c, 0, P));
+        int rr = h3d_fas_restrict(c, 0, P, s);
+        if (rr == HEAT3D_ENOTCONV) status = rr;
+        else if (rr < 0) return rr;
         int rc = coarse_pass(c, P, s);
         if (rc == HEAT3D_ENOTCONV) status = rc;
         else if (rc < 0) return rc;
@@ -1359,7 +1440,7 @@ int heat3d_set_node(heat3d_ctx* c, int level, int item, int node, const double* 
   double* dst = L.U + ((size_t)item * L.L.M + node) * L.g.fs;
   RET(h3d_load_dense(c, level, in, dst));
   CK(launch_lap(L.L.order, L.g, 1, dst, 0, L.F + ((size_t)item * L.L.M + node) * L.g.fs, 0,
-                L.alpha_items + item, nullptr, nullptr, 0, nullptr, L.shape64, c->st));
+                L.alpha_items + item, nullptr, nullptr, 0, nullptr, L.shape64, c->st, wu_of(L, dst)));
   CK(cudaStreamSynchronize(c->st));
   return HEAT3D_OK;
 }
@@ -1389,9 +1470,10 @@ int heat3d_fas_restrict(heat3d_ctx* c, int begin, int count) {
   NEED_BOUND(c);
   if (c->cfg.nlevels != 2 || begin < 0 || count < 1 || begin + count > c->lv[0].B)
     return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
-  RET(h3d_fas_restrict(c, begin, count));
+  int rc = h3d_fas_restrict(c, begin, count, nullptr);
+  if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
   CK(cudaStreamSynchronize(c->st));
-  return HEAT3D_OK;
+  return rc;
 }
 
 int heat3d_fas_interpolate(heat3d_ctx* c, int begin, int count) {

@@ -30,13 +30,16 @@ struct SdcLevel {
   // device buffers (workspace); node fields are [item][node] at stride g.fs
   double *U = nullptr, *F = nullptr, *I = nullptr;
   double *tauS = nullptr, *UGr = nullptr, *qF = nullptr, *D = nullptr;  // coarse level only
+  // compact stencil only: W U at every node (layout of U), and per item the
+  // weighted residual that the FAS restriction's W-solve takes as rhs
+  double *WU = nullptr, *Wr = nullptr;
   double *abi_u = nullptr, *abi_b = nullptr, *abi_p0 = nullptr, *abi_p1 = nullptr;
   MgBufs mgb[kMaxLevels];
   double* phi = nullptr;  // sin(pi x_i), i = 1..N
   double* alpha_items = nullptr;
   double* alpha_nodes = nullptr;
   ItemSDC* items_d = nullptr;
-  int nslots = 0;
+  int nslots = 0;   // M - 1 substeps, mg_vcycle calls (slot M - 1), W-solve (slot M)
   void* coefT = nullptr;  // Coef<T>[slot][mg level][item]
   Coef<double>* coef64 = nullptr;  // Coef<double>[slot][item], finest multigrid level
   unsigned long long* norms = nullptr;
@@ -110,7 +113,7 @@ int h3d_mg_solve(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, lon
 int h3d_eval_F(heat3d_ctx* c, int lev, int b0, int B);
 int h3d_residual(heat3d_ctx* c, int lev, int b0, int B, double* res, std::vector<double>* per_item);
 int h3d_sweep(heat3d_ctx* c, int lev, int b0, int B, double check_tol, heat3d_stats* s);
-int h3d_fas_restrict(heat3d_ctx* c, int b0, int B);
+int h3d_fas_restrict(heat3d_ctx* c, int b0, int B, heat3d_stats* s = nullptr);
 int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B);
 int h3d_spread(heat3d_ctx* c, int lev, int b0, int B, const double* u);
 int h3d_run(heat3d_ctx* c, double* ucur, heat3d_stats* s);

@@ -71,12 +71,15 @@ __global__ void k_integrals(Grid g, const double* __restrict__ U, const double* 
 
 // Coarse point (I, J, K) (0-based) sits on fine point (2I+1, 2J+1, 2K+1), or on
 // the same point when the two grids are equal.
+// X (compact fine level): qF_m = R(U_jm - U_0 + X_{m-1}) with X_{m-1} = W^{-1} r
+// of coarse node m >= 1 (field m-1 of each item at item stride xs), qF_0 = 0.
 template <int MF, int MG>
 __global__ void k_fas_inject(Grid gf, Grid gg, int same, const double* __restrict__ UF,
                              const double* __restrict__ FF, double* __restrict__ UG,
                              double* __restrict__ UGr, double* __restrict__ qF,
                              const ItemSDC* __restrict__ itF, const FasMap* __restrict__ map,
-                             const double* __restrict__ phif1d) {
+                             const double* __restrict__ phif1d, const double* __restrict__ X,
+                             long long xs) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int b = blockIdx.z / gg.N;
@@ -99,11 +102,45 @@ __global__ void k_fas_inject(Grid gf, Grid gg, int same, const double* __restric
     const long long o = ((long long)b * MG + m) * gg.fs + gidx;
     UG[o] = v;
     UGr[o] = v;
+    if (X) {
+      qF[o] = m == 0 ? 0.0 : (v - UFb[0]) + X[(long long)b * xs + (long long)(m - 1) * gf.fs + fidx];
+      continue;
+    }
     double q = it.gQ[jm] * phi;
 #pragma unroll
     for (int p = 0; p < MF; ++p) q = fma(it.dtQ[jm][p], Fq[p], q);
     qF[o] = q;
   }
+}
+
+// Compact fine level, coarse node m (fine node jm): the weighted residual
+// r = W U_0 + dt sum_p Q[jm][p] (F_p + W f_p) - W U_jm on the fine grid, into
+// R (one field per item) and into X (the W-solve's start value, item stride
+// xs); max |r| per item into res_bits.
+template <int MF>
+__global__ void k_fas_wresid(Grid gf, int jm, const double* __restrict__ WU,
+                             const double* __restrict__ FF, const ItemSDC* __restrict__ itF,
+                             const double* __restrict__ phif1d, double* __restrict__ R,
+                             double* __restrict__ X, long long xs, unsigned long long* res_bits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int b = blockIdx.z / gf.N;
+  const int k = blockIdx.z - b * gf.N;
+  unsigned long long mx = 0ull;
+  if (i < gf.N && j < gf.N) {
+    const long long idx = (long long)k * gf.plane + (long long)j * gf.px + i;
+    const double* Wb = WU + (long long)b * MF * gf.fs + idx;
+    const double* Fb = FF + (long long)b * MF * gf.fs + idx;
+    const ItemSDC& it = itF[b];
+    double q = it.gQ[jm] * (phif1d[i] * phif1d[j] * phif1d[k]);
+#pragma unroll
+    for (int p = 0; p < MF; ++p) q = fma(it.dtQ[jm][p], Fb[p * gf.fs], q);
+    const double r = (Wb[0] + q) - Wb[jm * gf.fs];
+    R[(long long)b * gf.fs + idx] = r;
+    X[(long long)b * xs + idx] = r;
+    mx = abs_bits(r);
+  }
+  warp_max_to(mx, res_bits + b);
 }
 
 template <int MG>
@@ -182,20 +219,38 @@ cudaError_t launch_integrals(int M, const Grid& g, int B, const double* U, const
 cudaError_t launch_fas_inject(int MF, int MG, const Grid& gf, const Grid& gg, int B,
                               const double* UF, const double* FF, double* UG, double* UGr,
                               double* qF, const ItemSDC* itF, const FasMap* map,
-                              const double* phif1d, cudaStream_t st) {
+                              const double* phif1d, cudaStream_t st, const double* X,
+                              long long xs) {
   if (B <= 0) return cudaSuccess;
   int same = gf.N == gg.N;
   dim3 grd = point_grid(gg, B), blk(32, 8);
-#define X(a, b)                                                                         \
+#define X_(a, b)                                                                        \
   if (MF == a && MG == b) {                                                             \
     k_fas_inject<a, b><<<grd, blk, 0, st>>>(gf, gg, same, UF, FF, UG, UGr, qF, itF, map, \
-                                            phif1d);                                    \
+                                            phif1d, X, xs);                             \
     count_launch();                                                                     \
     return cudaGetLastError();                                                          \
   }
-  H3D_FAS_CASES(X)
-#undef X
+  H3D_FAS_CASES(X_)
+#undef X_
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_fas_wresid(int MF, const Grid& gf, int B, int jm, const double* WU,
+                              const double* FF, const ItemSDC* itF, const double* phif1d,
+                              double* R, double* X, long long xs, unsigned long long* res_bits,
+                              cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  dim3 grd = point_grid(gf, B), blk(32, 8);
+  switch (MF) {
+    case 2: k_fas_wresid<2><<<grd, blk, 0, st>>>(gf, jm, WU, FF, itF, phif1d, R, X, xs, res_bits); break;
+    case 3: k_fas_wresid<3><<<grd, blk, 0, st>>>(gf, jm, WU, FF, itF, phif1d, R, X, xs, res_bits); break;
+    case 4: k_fas_wresid<4><<<grd, blk, 0, st>>>(gf, jm, WU, FF, itF, phif1d, R, X, xs, res_bits); break;
+    case 5: k_fas_wresid<5><<<grd, blk, 0, st>>>(gf, jm, WU, FF, itF, phif1d, R, X, xs, res_bits); break;
+    default: return cudaErrorInvalidValue;
+  }
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fas_tau(int MG, const Grid& gg, int B, const double* qF, const double* FG,

@@ -104,11 +104,22 @@ __device__ __forceinline__ T combine(T s1, T s2) {
   return fma(T(16), s1, -s2);
 }
 
+// b - A u at one point from the centre c and the neighbour sums s1, s2 (for
+// the compact stencil: faces and edges, A u = d c - e s1 - e2 s2).
+template <typename T, int ORDER>
+__device__ __forceinline__ T a_res(T d, T e, T e2, T c, T s1, T s2, T b) {
+  if (ORDER == kCompact) return fma(-d, c, fma(e, s1, fma(e2, s2, b)));
+  return fma(-d, c, fma(e, combine<T, ORDER>(s1, s2), b));
+}
+
 // ---------------------------------------------------------------------------
 // operators
 // ---------------------------------------------------------------------------
 
 // F = alpha_b L u (and, when ADD, the next substep's rhs add_dst = u + add_src).
+// Compact stencil: F = alpha_b (-24 u + 2 S1 + S2) with alpha = nu / (6 h^2);
+// the weighted field W u = (6 u + S1) / 12 is written to wu (when given) and
+// replaces u in the rhs, add_dst = W u + add_src.
 // Operators take 32-bit offsets within the item (fields are < 2^31 elements);
 // init(b) resolves the item's base pointers once.  Optional outputs are
 // template parameters so that unused FP64 work is not executed.
@@ -124,6 +135,8 @@ struct OpLap {
   double* o_;
   const double* as_;
   double* ad_;
+  double* wu;  // compact stencil: optional W u output, stride us
+  double* wu_;
   __device__ const double* src(int b) const { return u + b * us; }
   __device__ void init(int b) {
     a = alpha[b];
@@ -132,6 +145,7 @@ struct OpLap {
       as_ = add_src + b * as;
       ad_ = add_dst + b * as;
     }
+    if (ORDER == kCompact) wu_ = wu ? wu + b * us : nullptr;
   }
   __device__ Ex load(int idx) const {
     Ex x;
@@ -139,6 +153,13 @@ struct OpLap {
     return x;
   }
   __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
+    if (ORDER == kCompact) {
+      o_[idx] = a * fma(-24.0, c, fma(2.0, s1, s2));
+      const double w = fma(6.0, c, s1) * (1.0 / 12.0);
+      if (wu_) wu_[idx] = w;
+      if (ADD) ad_[idx] = w + ex.add;
+      return 0.0;
+    }
     double L = ORDER == 2 ? fma(-6.0, c, s1) : fma(-90.0, c, fma(16.0, s1, -s2));
     o_[idx] = a * L;
     if (ADD) ad_[idx] = c + ex.add;
@@ -159,10 +180,12 @@ struct OpResid64 {
   const double* b_;
   TR* r_;
   TR* e0_;
+  double e2;
   __device__ const double* src(int b) const { return u + b * us; }
   __device__ void init(int b) {
     d = coef[b].d;
     e = coef[b].e;
+    e2 = coef[b].e2;
     wd = e0 ? coef_r[b].wd : TR(0);
     b_ = bb + b * bs;
     r_ = r + b * rs;
@@ -170,8 +193,7 @@ struct OpResid64 {
   }
   __device__ Ex load(int idx) const { return Ex{b_[idx]}; }
   __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
-    double S = combine<double, ORDER>(s1, s2);
-    double res = fma(-d, c, fma(e, S, ex.b));
+    double res = a_res<double, ORDER>(d, e, e2, c, s1, s2, ex.b);
     TR rt = (TR)res;
     r_[idx] = rt;
     if (e0_) e0_[idx] = wd * rt;
@@ -194,11 +216,13 @@ struct OpJacobi {
   const T* r_;
   T* o_;
   double* u_;
+  T e2c;
   __device__ const T* src(int b) const { return e + b * fs; }
   __device__ void init(int b) {
     d = coef[b].d;
     ec = coef[b].e;
     wd = coef[b].wd;
+    e2c = coef[b].e2;
     r_ = r + b * fs;
     if (UPD) u_ = u64 + b * u64s;
     else o_ = out + b * fs;
@@ -210,8 +234,7 @@ struct OpJacobi {
     return x;
   }
   __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
-    T S = combine<T, ORDER>(s1, s2);
-    T res = fma(-d, c, fma(ec, S, ex.r));
+    T res = a_res<T, ORDER>(d, ec, e2c, c, s1, s2, ex.r);
     T v = fma(wd, res, c);
     if (UPD) u_[idx] = ex.u + (double)v;
     else o_[idx] = v;
@@ -220,7 +243,7 @@ struct OpJacobi {
   // Four consecutive x points (FP32 storage, k_tile4): idx is a multiple of
   // 4, n >= 1 of the four are inside the grid.  Same arithmetic per point as
   // apply().
-  static constexpr bool kVec4 = sizeof(TT) == 4;
+  static constexpr bool kVec4 = sizeof(TT) == 4 && ORDER != kCompact;
   static constexpr int kRegFloor = UPD ? 96 : 64;  // registers k_tile4 keeps without spilling
   struct Ex4 { float4 r; double2 u01, u23; };
   __device__ Ex4 load4(int idx) const {
@@ -273,20 +296,21 @@ struct OpResid {
   T d, ec;
   const T* r_;
   T* o_;
+  T e2c;
   __device__ const T* src(int b) const { return e + b * fs; }
   __device__ void init(int b) {
     d = coef[b].d;
     ec = coef[b].e;
+    e2c = coef[b].e2;
     r_ = r + b * fs;
     o_ = rr + b * fs;
   }
   __device__ Ex load(int idx) const { return Ex{r_[idx]}; }
   __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
-    T S = combine<T, ORDER>(s1, s2);
-    o_[idx] = fma(-d, c, fma(ec, S, ex.r));
+    o_[idx] = a_res<T, ORDER>(d, ec, e2c, c, s1, s2, ex.r);
     return 0.0;
   }
-  static constexpr bool kVec4 = sizeof(TT) == 4;
+  static constexpr bool kVec4 = sizeof(TT) == 4 && ORDER != kCompact;
   static constexpr int kRegFloor = 64;
   struct Ex4 { float4 r; };
   __device__ Ex4 load4(int idx) const { return Ex4{*reinterpret_cast<const float4*>(r_ + idx)}; }
@@ -317,7 +341,7 @@ template <int ORDER, bool NORM, typename Op>
 __global__ void __launch_bounds__(128) k_zmarch(Grid g, int nzc, int zc, const int* active,
                                                 unsigned long long* norm_bits, Op op) {
   using T = typename Op::T;
-  constexpr int R = ORDER == 2 ? 1 : 2;
+  constexpr int R = ORDER == 4 ? 2 : 1;
   const int b = blockIdx.z / nzc;
   if (active && !active[b]) return;  // uniform over the block
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -342,6 +366,13 @@ __global__ void __launch_bounds__(128) k_zmarch(Grid g, int nzc, int zc, const i
       if (R == 2)
         s2 = ((at(u, g, i - 2, j, k) + at(u, g, i + 2, j, k)) +
               (at(u, g, i, j - 2, k) + at(u, g, i, j + 2, k))) + (q[0] + q[2 * R]);
+      if (ORDER == kCompact)  // the 12 edge neighbours, grouped xy, xz, yz
+        s2 = (((at(u, g, i - 1, j - 1, k) + at(u, g, i + 1, j - 1, k)) +
+               (at(u, g, i - 1, j + 1, k) + at(u, g, i + 1, j + 1, k))) +
+              ((at(u, g, i - 1, j, k - 1) + at(u, g, i + 1, j, k - 1)) +
+               (at(u, g, i - 1, j, k + 1) + at(u, g, i + 1, j, k + 1)))) +
+             ((at(u, g, i, j - 1, k - 1) + at(u, g, i, j + 1, k - 1)) +
+              (at(u, g, i, j - 1, k + 1) + at(u, g, i, j + 1, k + 1)));
       double rv = o.apply(idx, q[R], s1, s2, ex);
       if (NORM) {
         unsigned long long bits = abs_bits(rv);
@@ -362,7 +393,7 @@ __host__ __device__ constexpr int halo_x() { return 16 / (int)sizeof(T); }
 // read, and the slot refilled during the current plane.
 template <typename T, int ORDER, int TYT, int RY, int D>
 constexpr int tile_smem_bytes() {
-  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) *
+  return (2 * (ORDER == 4 ? 2 : 1) + D + 1) * (TYT * RY + 2 * (ORDER == 4 ? 2 : 1)) *
          (32 + 2 * halo_x<T>()) * (int)sizeof(T);
 }
 
@@ -373,7 +404,7 @@ template <int ORDER, int TYT, int RY, int D, bool NORM, typename Op>
 __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, const int* active,
                                                    unsigned long long* norm_bits, Op op) {
   using T = typename Op::T;
-  constexpr int R = ORDER == 2 ? 1 : 2;
+  constexpr int R = ORDER == 4 ? 2 : 1;
   constexpr int TX = 32, TY = TYT * RY;
   constexpr int XH = halo_x<T>();
   constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D + 1;
@@ -463,12 +494,34 @@ __global__ void __launch_bounds__(32 * TYT) k_tile(Grid g, int nzc, int zc, cons
         xm2 = P0[o0 - 2]; xp2 = P0[o0 + 2]; ym2 = P0[o0 - 2 * SX]; yp2 = P0[o0 + 2 * SX];
         zm2 = Pm2[o0]; zp2 = Pp2[o0];
       }
+      const bool yedge = j < R || j >= N - R;
       if (xedge) fix_axis<T, R>(i, N, c, xm1, xp1, xm2, xp2);
-      if (j < R || j >= N - R) fix_axis<T, R>(j, N, c, ym1, yp1, ym2, yp2);
+      if (yedge) fix_axis<T, R>(j, N, c, ym1, yp1, ym2, yp2);
       if (zedge) fix_axis<T, R>(k, N, c, zm1, zp1, zm2, zp2);
       T s1 = ((xm1 + xp1) + (ym1 + yp1)) + (zm1 + zp1);
       T s2 = T(0);
       if (R == 2) s2 = ((xm2 + xp2) + (ym2 + yp2)) + (zm2 + zp2);
+      if (ORDER == kCompact) {
+        // edge neighbours e<axes>_<sign of first axis><sign of second axis>
+        T exy_mm = P0[o0 - SX - 1], exy_pm = P0[o0 - SX + 1];
+        T exy_mp = P0[o0 + SX - 1], exy_pp = P0[o0 + SX + 1];
+        T exz_mm = Pm1[o0 - 1], exz_pm = Pm1[o0 + 1], exz_mp = Pp1[o0 - 1], exz_pp = Pp1[o0 + 1];
+        T eyz_mm = Pm1[o0 - SX], eyz_pm = Pm1[o0 + SX], eyz_mp = Pp1[o0 - SX], eyz_pp = Pp1[o0 + SX];
+        if (xedge) {
+          if (i == 0) exy_mm = exy_mp = exz_mm = exz_mp = T(0);
+          if (i == N - 1) exy_pm = exy_pp = exz_pm = exz_pp = T(0);
+        }
+        if (yedge) {
+          if (j == 0) exy_mm = exy_pm = eyz_mm = eyz_mp = T(0);
+          if (j == N - 1) exy_mp = exy_pp = eyz_pm = eyz_pp = T(0);
+        }
+        if (zedge) {
+          if (k == 0) exz_mm = exz_pm = eyz_mm = eyz_pm = T(0);
+          if (k == N - 1) exz_mp = exz_pp = eyz_mp = eyz_pp = T(0);
+        }
+        s2 = (((exy_mm + exy_pm) + (exy_mp + exy_pp)) + ((exz_mm + exz_pm) + (exz_mp + exz_pp))) +
+             ((eyz_mm + eyz_pm) + (eyz_mp + eyz_pp));
+      }
       if (i < N && j < N) {
         double rv = o.apply(idx0 + r * g.px, c, s1, s2, ex[r]);
         if (NORM) {
@@ -513,7 +566,7 @@ cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active
 // same order as k_tile and k_zmarch, so the results are bitwise identical.
 template <int ORDER, int TYT, int RY, int D>
 constexpr int tile4_smem() {
-  return (2 * (ORDER == 2 ? 1 : 2) + D + 1) * (TYT * RY + 2 * (ORDER == 2 ? 1 : 2)) * (128 + 8) * 4;
+  return (2 * (ORDER == 4 ? 2 : 1) + D + 1) * (TYT * RY + 2 * (ORDER == 4 ? 2 : 1)) * (128 + 8) * 4;
 }
 // Blocks per SM that the ring allows, but no more than keeps the operator's
 // register floor (kRegFloor) available: the register cap that keeps them
@@ -530,7 +583,7 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
     k_tile4(Grid g, int nzc, int zc, const int* active, Op op) {
   using T = typename Op::T;
   static_assert(sizeof(T) == 4, "k_tile4 is the FP32 path");
-  constexpr int R = ORDER == 2 ? 1 : 2;
+  constexpr int R = ORDER == 4 ? 2 : 1;
   constexpr int TX = 128, TY = TYT * RY;
   constexpr int XH = 4;
   constexpr int SX = TX + 2 * XH, SY = TY + 2 * R, NB = 2 * R + D + 1;
@@ -761,7 +814,17 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
 cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long long u_stride,
                        double* out, long long out_stride, const double* alpha,
                        const double* add_src, double* add_dst, long long add_stride,
-                       const int* active, Shape sh, cudaStream_t st) {
+                       const int* active, Shape sh, cudaStream_t st, double* wu_out) {
+  if (order == kCompact) {
+    if (add_src) {
+      OpLap<kCompact, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+      op.wu = wu_out;
+      return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+    }
+    OpLap<kCompact, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
+    op.wu = wu_out;
+    return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (add_src) {
     if (order == 2) {
       OpLap<2, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
@@ -784,6 +847,11 @@ cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, lon
                            TR* r_out, TR* e0_out, const Coef<TR>* coef_r,
                            unsigned long long* norm_bits, const int* active, Shape sh,
                            cudaStream_t st) {
+  if (order == kCompact) {
+    OpResid64<kCompact, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+    return norm_bits ? run_stencil<kCompact, true>(g, B, active, norm_bits, op, sh, st)
+                     : run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (order == 2) {
     OpResid64<2, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
     return norm_bits ? run_stencil<2, true>(g, B, active, norm_bits, op, sh, st)
@@ -798,6 +866,14 @@ template <typename T>
 cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
                           double* u64, long long u64_stride, const Coef<T>* coef,
                           const int* active, Shape sh, cudaStream_t st) {
+  if (order == kCompact) {
+    if (u64) {
+      OpJacobi<T, kCompact, true> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+      return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+    }
+    OpJacobi<T, kCompact, false> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
+    return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (u64) {
     if (order == 2) {
       OpJacobi<T, 2, true> op{e, r, out, g.fs, u64, u64_stride, coef, T(0), T(0), T(0)};
@@ -817,6 +893,10 @@ cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* 
 template <typename T>
 cudaError_t launch_resid(int order, const Grid& g, int B, const T* e, const T* r, T* rr,
                          const Coef<T>* coef, const int* active, Shape sh, cudaStream_t st) {
+  if (order == kCompact) {
+    OpResid<T, kCompact> op{e, r, rr, g.fs, coef, T(0), T(0)};
+    return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
+  }
   if (order == 2) {
     OpResid<T, 2> op{e, r, rr, g.fs, coef, T(0), T(0)};
     return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);

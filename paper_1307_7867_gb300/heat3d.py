@@ -23,6 +23,7 @@ OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4,
 PROF_OFF, PROF_JACOBI_FINE, PROF_RESID64_FINE = 0, 1, 2
 FP64, MIXED = 0, 1
 FORCING_NONE, FORCING_PAPER_LITERAL, FORCING_EXACT = 0, 1, 2
+COMPACT = 19  # heat3d_level.order of the compact 19-point (Mehrstellen) fine stencil
 
 ABI_FUNCTIONS = [
     "heat3d_config_default", "heat3d_workspace_size", "heat3d_init", "heat3d_bind_workspace",
