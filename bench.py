@@ -61,6 +61,18 @@ WORKLOADS = {
              "iteration, iterated to residual 1e-10 (<= 50 iterations)",
         fine=(255, 4, 5), coarse=(127, 2, 3), dt=0.1875, sweeps_fine=1, sweeps_coarse=1,
         slices=32, iters=50, tol_sdc=1e-10, mg_tol=1e-11, precision="fp64", steps=32, warmup=0),
+    "c2c": dict(
+        desc="two-level MLSDC with the paper's compact fine stencil: fine 255^3 compact "
+             "19-point M=5 / coarse 127^3 7-point M=3, dt=1/64, 2 fine sweeps per iteration, "
+             "residual 1e-10 (<= 20 iterations), V(2,1) to 1e-11",
+        fine=(255, 19, 5), coarse=(127, 2, 3), dt=1 / 64, sweeps_fine=2, sweeps_coarse=1,
+        slices=1, iters=20, tol_sdc=1e-10, mg_tol=1e-11, precision="fp64", steps=6, warmup=3),
+    "paperc": dict(
+        desc="the paper's setup with its compact fine stencil: PFASST on 32 slices of "
+             "dt=0.1875 (T=6), fine 255^3 compact 19-point M=5 / coarse 127^3 7-point M=3, "
+             "1 fine sweep per iteration, iterated to residual 1e-10 (<= 50 iterations)",
+        fine=(255, 19, 5), coarse=(127, 2, 3), dt=0.1875, sweeps_fine=1, sweeps_coarse=1,
+        slices=32, iters=50, tol_sdc=1e-10, mg_tol=1e-11, precision="fp64", steps=32, warmup=0),
     "c4": dict(
         desc="mixed precision, fine 511^3 wide M=5 / coarse 255^3 7-point M=3, dt=1/32, "
              "MLSDC to residual 1e-10, FP32 V-cycles in FP64 refinement to 1e-11",
@@ -77,6 +89,16 @@ def analytic_amplitude(t, nu=0.1, kappa=1.0, lam=None):
     A = (1 + c * d) / (1 + c * c)
     B = (d - c) / (1 + c * c)
     return A * math.cos(t) + B * math.sin(t) + (1 - A) * math.exp(-c * t)
+
+
+def compact_lambda(N, nu=0.1):
+    """nu lam_L / lam_W of the compact scheme on the (1,1,1) sine mode: the
+    semi-discrete decay rate of W a' = nu L a + W f."""
+    h = 1.0 / (N + 1)
+    cs = math.cos(math.pi * h)
+    lam_l = (-24.0 + 12.0 * cs + 12.0 * cs * cs) / (6.0 * h * h)
+    lam_w = (3.0 + 3.0 * cs) / 6.0
+    return nu * lam_l / lam_w
 
 
 def wide_lambda(N, nu=0.1):
@@ -228,7 +250,9 @@ def run_ours(args, w, rank, world):
     tK = K * dt
     a_pde = analytic_amplitude(tK)
     err_pde = float(np.abs(uT - a_pde * phi).max() / abs(a_pde))
-    lam = wide_lambda(Nf) if w["fine"][1] == 4 else 0.1 * 3 * (2 * math.cos(math.pi / (Nf + 1)) - 2) * (Nf + 1) ** 2
+    order = w["fine"][1]
+    lam = (wide_lambda(Nf) if order == 4 else compact_lambda(Nf) if order == 19
+           else 0.1 * 3 * (2 * math.cos(math.pi / (Nf + 1)) - 2) * (Nf + 1) ** 2)
     a_sd = analytic_amplitude(tK, lam=lam)
     err_sd = float(np.abs(uT - a_sd * phi).max() / abs(a_sd))
 
