@@ -158,7 +158,7 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
-def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None):
+def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None, interp=None):
     prec = H.MIXED if (precision or w["precision"]) == "mixed" else H.FP64
     # mg_rel > 0: each solve stops at max(mg_tol, mg_rel x the sweep's incoming residual)
     mg_rel = w.get("mg_rel", 0.0) if mg_rel is None else mg_rel
@@ -168,7 +168,8 @@ def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None):
                          slices=slices or w["slices"], iters=w["iters"], tol_sdc=w["tol_sdc"],
                          mg_tol=w["mg_tol"], max_cycles=50, precision=prec,
                          forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"],
-                         use_graphs=1 if graphs else 0, autotune=1, inner=inner, mg_rel=mg_rel)
+                         use_graphs=1 if graphs else 0, autotune=1, inner=inner, mg_rel=mg_rel,
+                         interp=w.get("interp", 2) if interp is None else interp)
 
 
 def max_over_ranks(seconds, device, world):
@@ -305,6 +306,7 @@ def run_ours(args, w, rank, world):
         "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "f64+f32",
         "data": "synthetic (analytic initial value and forcing, Eqs. 3-4)",
         "config": {"workload": w["desc"], "N_fine": Nf, "dt": dt, "mg_rel": w.get("mg_rel", 0.0),
+                   "interp": w.get("interp", 2),
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "working set >> L2 (fields of 133 MB+), no flush needed"},
         "stats": {k: st[k] for k in ("vcycles", "vcycles_level", "solves", "sweeps", "iters",
@@ -328,13 +330,13 @@ def run_ours(args, w, rank, world):
 ADAPTIVE_REL = {"fp64": 0.01, "mixed": 0.02}
 
 
-def run_variant(args, w, u0, uT, out, precision, mg_rel):
+def run_variant(args, w, u0, uT, out, precision, mg_rel, interp=None):
     """The timed steps of the headline run again with another precision or
     solver-tolerance rule; accuracy against the PDE solution and the FP64 run."""
     import torch
     from paper_1307_7867_gb300 import heat3d as H, inputs
-    cm = H.Context(make_cfg(H, w, precision=precision, graphs=not args.no_graphs, mg_rel=mg_rel),
-                   stream=torch.cuda.Stream())
+    cm = H.Context(make_cfg(H, w, precision=precision, graphs=not args.no_graphs, mg_rel=mg_rel,
+                            interp=interp), stream=torch.cuda.Stream())
     u0_d = torch.from_numpy(u0).cuda()
     o = torch.empty_like(u0_d)
     if args.warmup > 0:
@@ -353,7 +355,7 @@ def run_variant(args, w, u0, uT, out, precision, mg_rel):
     a_pde = analytic_amplitude(args.steps * w["dt"])
     err_m = float(np.abs(um - a_pde * inputs.sine_mode(Nf)).max() / abs(a_pde))
     cm.close()
-    return {"precision": precision, "mg_rel": mg_rel,
+    return {"precision": precision, "mg_rel": mg_rel, "interp": interp or w.get("interp", 2),
             "value": Nf ** 3 * args.steps / s_m, "ms_per_step": s_m * 1e3 / args.steps,
             "rel_err_vs_pde_solution": err_m,
             "max_rel_diff_vs_fp64": float(np.abs(um - uT).max() / np.abs(uT).max()),
@@ -602,6 +604,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision and adaptive-tolerance variants")
+    ap.add_argument("--interp", type=int, default=None, choices=[2, 4],
+                    help="interpolation of the coarse correction: 2 trilinear, 4 cubic")
     ap.add_argument("--mg-rel", type=float, default=None,
                     help="headline run: solver tolerance max(mg_tol, MG_REL x sweep residual)")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
@@ -623,6 +627,8 @@ def main():
     if args.mg_rel:
         w = dict(w, mg_rel=args.mg_rel,
                  desc=w["desc"] + f"; solves stop at max(mg_tol, {args.mg_rel} x sweep residual)")
+    if args.interp == 4:
+        w = dict(w, interp=4, desc=w["desc"] + "; cubic interpolation of the coarse correction")
     args.steps = args.steps or w["steps"]
     args.warmup = w["warmup"] if args.warmup is None else args.warmup
     if args.warmup < 3 and w["slices"] == 1:
@@ -653,6 +659,10 @@ def main():
         out["mixed"] = run_variant(args, w, u0, uT, out, "mixed", 0.0)
         out["adaptive"] = run_variant(args, w, u0, uT, out, "fp64", ADAPTIVE_REL["fp64"])
         out["adaptive_mixed"] = run_variant(args, w, u0, uT, out, "mixed", ADAPTIVE_REL["mixed"])
+        # cubic interpolation of the coarse correction (heat3d_config.interp = 4)
+        out["cubic"] = run_variant(args, w, u0, uT, out, "fp64", 0.0, interp=4)
+        out["cubic_adaptive_mixed"] = run_variant(args, w, u0, uT, out, "mixed",
+                                                  ADAPTIVE_REL["mixed"], interp=4)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fv = st["vcycles_level"][0] / max(args.steps, 1)

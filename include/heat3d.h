@@ -108,6 +108,10 @@ typedef struct {
                                grids with N >= 16 instead (testing) */
   int fuse_coarse;          /* 1: run the multigrid levels with N <= 15 of a V-cycle in one
                                kernel, all levels in shared memory (results identical) */
+  int interp;               /* spatial interpolation of the coarse correction in the FAS
+                               step (Sec. 1.1; the paper does not say which): 2 trilinear
+                               (default), 4 tensor-product cubic (4-point midpoint rule,
+                               odd reflection at the boundary) */
 } heat3d_config;
 
 typedef struct {

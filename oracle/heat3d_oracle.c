@@ -60,6 +60,8 @@ typedef struct {
   int nu1, nu2;   /* pre- and post-smoothing sweeps, V(nu1, nu2) */
   double mg_rel;  /* > 0: a sweep's solves stop at max(mg_tol, mg_rel * residual of the
                      sweep's incoming iterate) */
+  int interp;     /* spatial interpolation of the FAS correction: 4 = cubic
+                     (4-point, odd reflection at the boundary), else trilinear */
 } or_problem;
 
 typedef struct {
@@ -260,6 +262,45 @@ void or_prolong_add(int Nc, const double* e, double* uf) {
               s += coarse_at(e, Nc, ia[a], ja[b], ka[c]) / (double)(ni * nj * nk);
         uf[id3(Nf, i, j, k)] += s;
       }
+}
+
+/* One axis of the cubic interpolation: value at fine index i (1..2Nc+1) from
+ * the coarse line e(1..Nc) with zero boundary values and odd reflection
+ * beyond them: even i take the coarse value, odd i the 4-point Lagrange
+ * midpoint (-e(I-1) + 9 e(I) + 9 e(I+1) - e(I+2)) / 16. */
+static double cubic_line_at(const double* e, int stride, int Nc, int i) {
+  if (i % 2 == 0) return e[(size_t)(i / 2 - 1) * stride];
+  int I = (i - 1) / 2;
+  double v[4];
+  for (int q = 0; q < 4; ++q) {
+    int a = I - 1 + q;
+    double sgn = 1.0;
+    if (a == 0 || a == Nc + 1) { v[q] = 0.0; continue; }
+    if (a < 0) { a = -a; sgn = -1.0; }
+    if (a > Nc + 1) { a = 2 * (Nc + 1) - a; sgn = -1.0; }
+    v[q] = sgn * e[(size_t)(a - 1) * stride];
+  }
+  return (-v[0] + 9.0 * v[1] + 9.0 * v[2] - v[3]) / 16.0;
+}
+
+/* uf += P3 e: tensor-product cubic interpolation, x, then y, then z. */
+void or_prolong_add_cubic(int Nc, const double* e, double* uf) {
+  int Nf = 2 * Nc + 1;
+  double* tx = (double*)malloc((size_t)Nf * Nc * Nc * sizeof(double));
+  double* txy = (double*)malloc((size_t)Nf * Nf * Nc * sizeof(double));
+  for (int K = 0; K < Nc; ++K)
+    for (int J = 0; J < Nc; ++J)
+      for (int i = 1; i <= Nf; ++i)
+        tx[((size_t)K * Nc + J) * Nf + (i - 1)] = cubic_line_at(e + ((size_t)K * Nc + J) * Nc, 1, Nc, i);
+  for (int K = 0; K < Nc; ++K)
+    for (int j = 1; j <= Nf; ++j)
+      for (int i = 0; i < Nf; ++i)
+        txy[((size_t)K * Nf + (j - 1)) * Nf + i] = cubic_line_at(tx + (size_t)K * Nc * Nf + i, Nf, Nc, j);
+  for (int k = 1; k <= Nf; ++k)
+    for (int j = 0; j < Nf; ++j)
+      for (int i = 0; i < Nf; ++i)
+        uf[((size_t)(k - 1) * Nf + j) * Nf + i] += cubic_line_at(txy + (size_t)j * Nf + i, Nf * Nf, Nc, k);
+  free(tx); free(txy);
 }
 
 /* Exact solve on the one-unknown grid: A11 is read off by applying A to the
@@ -694,6 +735,8 @@ int or_fas_interpolate(const or_level* LF, const or_level* LG, const or_problem*
     }
     if (NF == NG) {
       for (size_t p = 0; p < nf; ++p) UF[(size_t)j * nf + p] += d[p];
+    } else if (P->interp == 4) {
+      or_prolong_add_cubic(NG, d, UF + (size_t)j * nf);
     } else {
       or_prolong_add(NG, d, UF + (size_t)j * nf);
     }

@@ -41,7 +41,7 @@ class Level(C.Structure):
 class Problem(C.Structure):
     _fields_ = [("nu", C.c_double), ("forcing", C.c_int), ("kappa", C.c_double),
                 ("mg_tol", C.c_double), ("mg_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
-                ("mg_rel", C.c_double)]
+                ("mg_rel", C.c_double), ("interp", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -73,6 +73,7 @@ def lib():
         L.or_jacobi.argtypes = [I, I, D, _dp, _dp, _dp]
         L.or_restrict_fw.argtypes = [I, _dp, _dp]
         L.or_prolong_add.argtypes = [I, _dp, _dp]
+        L.or_prolong_add_cubic.argtypes = [I, _dp, _dp]
         L.or_vcycle.argtypes = [I, I, D, _dp, _dp, I, I]
         L.or_mg_solve.argtypes = [I, I, D, _dp, _dp, D, I, I, I, P(I), P(D)]
         L.or_mg_solve.restype = I
@@ -168,6 +169,14 @@ def prolong_add(e, uf):
     return uf
 
 
+def prolong_add_cubic(e, uf):
+    """uf += tensor-product cubic (4-point) interpolation of e (FAS correction, interp = 4)."""
+    e = _c(e)
+    uf = _c(uf).copy()
+    lib().or_prolong_add_cubic(e.shape[0], e, uf)
+    return uf
+
+
 def vcycle(u, b, order, c, nu1=2, nu2=1):
     u = _c(u).copy()
     b = _c(b)
@@ -229,10 +238,11 @@ class Prob:
     nu1: int = 2
     nu2: int = 1
     mg_rel: float = 0.0
+    interp: int = 2
 
     def c(self):
         return Problem(self.nu, self.forcing, self.kappa, self.mg_tol, self.mg_max, self.nu1,
-                       self.nu2, self.mg_rel)
+                       self.nu2, self.mg_rel, self.interp)
 
 
 def spread(N, order, M, prob: Prob, u0):

@@ -77,6 +77,14 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
                                long long ec_stride, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st);
 
+// uf += tensor-product cubic interpolation of ec (the FAS correction with
+// heat3d_config.interp = 4): along each axis even fine points take the
+// coarse value, odd ones (-e(I-1) + 9 e(I) + 9 e(I+1) - e(I+2)) / 16 with zero
+// boundary values and odd reflection beyond them.  FP64, B fields.
+cudaError_t launch_prolong_add_cubic(const Grid& gc, const Grid& gf, int B, const double* ec,
+                                     long long ec_stride, double* uf, long long uf_stride,
+                                     cudaStream_t st);
+
 // The whole V-cycle below (and including) a level with N <= 15, one block per
 // item, every level in shared memory (coarse_fused.cu).  Ns: sizes from that
 // level down to 1; cf[l]: coefficients of level l for item 0 of the launch;

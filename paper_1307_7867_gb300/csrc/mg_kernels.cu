@@ -170,6 +170,67 @@ __global__ void k_prolong_add(Grid gc, Grid gf, const T* __restrict__ ec, long l
   }
 }
 
+// Taps of the cubic interpolation along one axis for fine index f (0-based):
+// even 1-based fine points take their coarse point, odd ones the 4-point
+// midpoint weights (-1, 9, 9, -1) / 16; coarse points 0 and Nc + 1 (1-based)
+// are the zero boundary, points beyond are odd reflections.  Always four
+// taps (unused ones weigh 0, index kept valid) so that they stay in registers.
+__device__ __forceinline__ void cubic_taps(int f, int Nc, int (&ix)[4], double (&w)[4]) {
+  const int f1 = f + 1;
+  if ((f1 & 1) == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ix[q] = f1 / 2 - 1;
+      w[q] = q == 0 ? 1.0 : 0.0;
+    }
+    return;
+  }
+  const int I = (f1 - 1) / 2;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int a = I - 1 + q;
+    double cw = (q == 1 || q == 2) ? 9.0 / 16.0 : -1.0 / 16.0;
+    if (a == 0 || a == Nc + 1) { cw = 0.0; a = 1; }
+    if (a < 0) { a = -a; cw = -cw; }
+    if (a > Nc + 1) { a = 2 * (Nc + 1) - a; cw = -cw; }
+    ix[q] = a - 1;
+    w[q] = cw;
+  }
+}
+
+// uf += P3 ec: one thread per fine point, separable sums x, then y, then z
+// (zero-weight taps are skipped).
+__global__ void k_prolong_cubic(Grid gc, Grid gf, const double* __restrict__ ec, long long ecs,
+                                double* __restrict__ uf, long long ufs) {
+  PointIdx p;
+  if (!point_index(gf, p)) return;
+  int xi[4], yi[4], zi[4];
+  double xw[4], yw[4], zw[4];
+  cubic_taps(p.i, gc.N, xi, xw);
+  cubic_taps(p.j, gc.N, yi, yw);
+  cubic_taps(p.k, gc.N, zi, zw);
+  const double* e = ec + p.b * ecs;
+  double sz = 0.0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    if (zw[c] == 0.0) continue;
+    double sy = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      if (yw[b] == 0.0) continue;
+      const double* row = e + (long long)zi[c] * gc.plane + (long long)yi[b] * gc.px;
+      double sx = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+        if (xw[a] != 0.0) sx = fma(xw[a], __ldg(row + xi[a]), sx);
+      sy = fma(yw[b], sx, sy);
+    }
+    sz = fma(zw[c], sy, sz);
+  }
+  double* o = uf + p.b * ufs + p.idx;
+  *o = *o + sz;
+}
+
 template <typename T>
 __global__ void k_update(Grid g, const T* __restrict__ e, double* __restrict__ u, long long us,
                          const int* active) {
@@ -247,6 +308,15 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
   const int nc1 = gc.N + 1;
   k_prolong_add<T><<<dim3((nc1 + 31) / 32, (nc1 + 7) / 8, nc1 * B), dim3(32, 8), 0, st>>>(
       gc, gf, ec, ec_stride, uf, uf_stride, active);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add_cubic(const Grid& gc, const Grid& gf, int B, const double* ec,
+                                     long long ec_stride, double* uf, long long uf_stride,
+                                     cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  k_prolong_cubic<<<point_grid(gf, B), dim3(32, 8), 0, st>>>(gc, gf, ec, ec_stride, uf, uf_stride);
   count_launch();
   return cudaGetLastError();
 }

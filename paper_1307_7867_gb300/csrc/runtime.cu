@@ -194,6 +194,8 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
     return h3d_fail(c, HEAT3D_EINVAL, "multigrid needs nu1 >= 1, nu2 >= 0, max_cycles >= 1");
   if (!(cfg->mg.rel >= 0 && cfg->mg.rel < 1))
     return h3d_fail(c, HEAT3D_EINVAL, "mg.rel must lie in [0, 1)");
+  if (cfg->interp != 0 && cfg->interp != 2 && cfg->interp != 4)
+    return h3d_fail(c, HEAT3D_EINVAL, "interp must be 2 (trilinear) or 4 (cubic)");
   if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED)
     return h3d_fail(c, HEAT3D_EINVAL, "precision must be HEAT3D_FP64 or HEAT3D_MIXED");
   if (cfg->slices < 1 || cfg->sweeps_fine < 0 || cfg->sweeps_coarse < 0 || cfg->iters < 0)
@@ -948,6 +950,8 @@ int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
                       c->map_d, st));
   if (F.L.N == G.L.N) {
     CK(launch_update<double>(F.g, B * MF, D, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
+  } else if (c->cfg.interp == 4) {
+    CK(launch_prolong_add_cubic(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
   } else {
     CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
   }
@@ -1244,6 +1248,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->use_graphs = 0;
   cfg->autotune = 1;
   cfg->fuse_coarse = 1;
+  cfg->interp = 2;
 }
 
 int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes) {

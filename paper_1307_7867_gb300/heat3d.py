@@ -58,7 +58,8 @@ class Config(C.Structure):
                 ("slices", C.c_int), ("iters", C.c_int), ("tol_sdc", C.c_double),
                 ("predictor", C.c_int), ("mg", MG), ("precision", C.c_int), ("forcing", C.c_int),
                 ("batch", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int), ("autotune", C.c_int), ("fuse_coarse", C.c_int)]
+                ("use_graphs", C.c_int), ("autotune", C.c_int), ("fuse_coarse", C.c_int),
+                ("interp", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -261,7 +262,7 @@ def pfasst_run(ctx: Context, u0, uT, allow_notconv=False):
 def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2, sweeps_coarse=1,
                 slices=1, iters=20, tol_sdc=1e-10, predictor=1, nu1=2, nu2=1, max_cycles=50,
                 mg_tol=1e-10, precision=FP64, forcing=FORCING_PAPER_LITERAL, batch=1, device=0,
-                use_graphs=0, autotune=1, inner=1, fuse_coarse=1, mg_rel=0.0) -> Config:
+                use_graphs=0, autotune=1, inner=1, fuse_coarse=1, mg_rel=0.0, interp=2) -> Config:
     """fine, coarse: (N, order, M) tuples; coarse None gives single-level SDC."""
     cfg = heat3d_config_default()
     cfg.nu, cfg.T, cfg.dt = nu, T, dt
@@ -276,6 +277,7 @@ def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2,
     cfg.use_graphs = use_graphs
     cfg.autotune = autotune
     cfg.fuse_coarse = fuse_coarse
+    cfg.interp = interp
     return cfg
 
 

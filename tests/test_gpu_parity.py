@@ -242,6 +242,41 @@ def test_adaptive_tolerance_rejects_bad_rel(H):
         cfg = H.make_config((15, 2, 3), dt=1 / 8, T=1 / 8, mg_rel=bad)
         with pytest.raises(H.Heat3DError):
             H.Context(cfg)
+    with pytest.raises(H.Heat3DError):
+        H.Context(H.make_config((15, 2, 3), dt=1 / 8, T=1 / 8, interp=3))
+    with pytest.raises(H.Heat3DError):  # the compact stencil is for the fine level only
+        H.Context(H.make_config((15, 4, 5), (7, H.COMPACT, 3), dt=1 / 8, T=1 / 8))
+
+
+@pytest.mark.parametrize("order", [4, 19])
+def test_run_mlsdc_cubic_correction_interpolation(H, oracle, order):
+    """interp = 4 (cubic interpolation of the coarse correction): same
+    iterations and V-cycles as the oracle, result to 1e-11."""
+    fine, coarse = (31, order, 5), (15, 2, 3)
+    cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
+                        mg_tol=1e-11, interp=4)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(31, seed=12, kmax=5)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, orc, ost = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11, interp=4), 1 / 64, 2,
+                                     u0, nsweeps_fine=2, max_iters=20, tol=1e-10)
+    assert st["iters"] == ost["iters"] and st["vcycles"] == ost["vcycles"]
+    assert rel(uT, ref) <= 1e-11
+
+
+def test_pfasst_cubic_interpolation_fixed_iterations(H, oracle):
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    P, K = 4, 3
+    cfg = H.make_config(fine, coarse, dt=1 / 8, T=P / 8, sweeps_fine=1, slices=P, iters=K,
+                        tol_sdc=-1.0, mg_tol=1e-12, interp=4)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(31, seed=13, kmax=4)
+    uT = np.empty_like(u0)
+    H.pfasst_run(ctx, u0, uT)
+    ref, _, _ = oracle.pfasst_run(fine, coarse, oracle.Prob(mg_tol=1e-12, interp=4), 1 / 8, P, P,
+                                  u0, nsweeps_fine=1, max_iters=K)
+    assert rel(uT, ref) <= 1e-11
 
 
 @pytest.mark.parametrize("P,K", [(4, 3), (8, 2)])

@@ -199,3 +199,35 @@ def test_compact_mg_contraction(oracle, N, ch2):
         r = np.abs(oracle.residual(u, b, oracle.COMPACT, c)).max()
         assert r <= 0.5 * prev
         prev = r
+
+
+# --------------------------------------------------------------------------
+# cubic interpolation of the FAS correction (option interp = 4)
+# --------------------------------------------------------------------------
+
+def test_cubic_interpolation_properties(oracle):
+    """Even fine points take the coarse values; away from the boundary the
+    tensor-product 4-point rule reproduces any cubic polynomial exactly
+    (numpy polynomial evaluation); on sin(pi x) (odd about both ends, as the
+    odd reflection assumes) the error falls like h^4."""
+    Nc = 7
+    Nf = 2 * Nc + 1
+    xc = np.arange(1, Nc + 1) / (Nc + 1)
+    xf = np.arange(1, Nf + 1) / (Nf + 1)
+    pc = [0.3, -1.2, 0.7, 2.0]  # a cubic, coefficients low -> high
+    px = lambda x: np.polynomial.polynomial.polyval(x, pc)
+    py = lambda x: np.polynomial.polynomial.polyval(x, [1.0, 0.5, -0.25, 0.125])
+    e = px(xc)[None, None, :] * py(xc)[None, :, None] * px(xc)[:, None, None]
+    out = oracle.prolong_add_cubic(e, np.zeros((Nf, Nf, Nf)))
+    ref = px(xf)[None, None, :] * py(xf)[None, :, None] * px(xf)[:, None, None]
+    inner = slice(3, Nf - 3)  # 4-point stencils that stay inside the coarse grid
+    assert np.abs(out[inner, inner, inner] - ref[inner, inner, inner]).max() <= 1e-13
+    assert np.array_equal(out[1::2, 1::2, 1::2], e)
+    errs = []
+    for nc in (7, 15, 31):
+        nf = 2 * nc + 1
+        ec = inputs.sine_mode(nc)
+        errs.append(np.abs(oracle.prolong_add_cubic(ec, np.zeros((nf, nf, nf))) -
+                           inputs.sine_mode(nf)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > 3.7), (errs, rates)

@@ -317,3 +317,19 @@ def test_compact_mlsdc_converges_to_sdc_collocation(oracle):
     b, rc2, _ = oracle.sdc_run(*fine, prob, 1 / 16, 2, 60, u0, tol=1e-12)
     assert rc == oracle.OK and rc2 == oracle.OK
     assert np.abs(a - b).max() <= 1e-10
+
+
+def test_cubic_correction_interpolation_converges_faster(oracle):
+    """MLSDC with the cubic interpolation of the coarse correction reaches the
+    same collocation solution as SDC, in fewer iterations than trilinear."""
+    fine, coarse = (15, 4, 5), (7, 2, 3)
+    u0 = inputs.sine_mode(15)
+    base = dict(nu=0.1, forcing=1, kappa=1.0, mg_tol=1e-13, mg_max=100)
+    a, rc, sa = oracle.mlsdc_run(fine, coarse, oracle.Prob(**base, interp=4), 1 / 16, 2, u0,
+                                 max_iters=60, tol=1e-12)
+    b, rc2, _ = oracle.sdc_run(*fine, oracle.Prob(**base), 1 / 16, 2, 60, u0, tol=1e-12)
+    c, rc3, sc = oracle.mlsdc_run(fine, coarse, oracle.Prob(**base), 1 / 16, 2, u0, max_iters=60,
+                                  tol=1e-12)
+    assert rc == rc2 == rc3 == oracle.OK
+    assert np.abs(a - b).max() <= 1e-10
+    assert sa["iters"] < sc["iters"]
