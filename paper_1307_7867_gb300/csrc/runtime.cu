@@ -94,9 +94,9 @@ void h3d_prof_end(heat3d_ctx* c, int pair, double bytes, double dpops, double fl
     return;
   }
   cudaEventRecord(c->prof_ev[2 * pair + 1], c->st);
-  c->prof_bytes += bytes;
-  c->prof_dpops += dpops;
-  c->prof_flops += flops;
+  c->prof_bytes += bytes * c->work_scale;
+  c->prof_dpops += dpops * c->work_scale;
+  c->prof_flops += flops * c->work_scale;
   c->prof_launches += 1;
 }
 
@@ -614,9 +614,9 @@ static void graph_harvest(heat3d_ctx* c, CycleGraph* g) {
     if (cudaEventElapsedTime(&ms, g->ev[p], g->ev[p + 1]) == cudaSuccess) c->prof_ms += ms;
     else cudaGetLastError();  // a failed timing read must not fail the next launch
   }
-  c->prof_bytes += g->prof_bytes;
-  c->prof_dpops += g->prof_dpops;
-  c->prof_flops += g->prof_flops;
+  c->prof_bytes += g->prof_bytes * c->work_scale;
+  c->prof_dpops += g->prof_dpops * c->work_scale;
+  c->prof_flops += g->prof_flops * c->work_scale;
   c->prof_launches += g->prof_launches;
 }
 
@@ -718,17 +718,21 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, one_cycle, &gph));
   }
   while (cycles < max_cycles && live > 0) {
+    c->work_scale = (double)live / B;  // converged items skip their blocks
     if (gph) {
       CK(cudaGraphLaunch(gph->exec, st));
       h3d::launches_adjust(gph->launches);
-      c->bytes += gph->bytes;
+      c->bytes += gph->bytes * c->work_scale;
       if (!gph->ev.empty()) {
         CK(cudaStreamSynchronize(st));
         graph_harvest(c, gph);
       }
     } else {
-      RET(one_cycle());
+      int rc = one_cycle();
+      if (rc < 0) c->work_scale = 1.0;
+      RET(rc);
     }
+    c->work_scale = 1.0;
     ++cycles;
     if (s) {
       s->vcycles += (long long)live * inner;

@@ -89,6 +89,9 @@ struct heat3d_ctx {
   std::vector<cudaEvent_t> prof_ev;  // pairs
   size_t prof_used = 0;              // pairs recorded and not yet harvested
   double prof_ms = 0.0, prof_bytes = 0.0, prof_dpops = 0.0, prof_flops = 0.0;
+  // fraction of a multigrid launch's items that are still iterating (items
+  // that have converged return at once): scales the profiled work
+  double work_scale = 1.0;
   long long prof_launches = 0;
   // CUDA graphs of V-cycles (cfg.use_graphs); `capturing` routes profiling
   // events into the graph being captured
