@@ -674,8 +674,6 @@ def main():
         out["cubic"] = run_variant(args, w, u0, uT, out, "fp64", 0.0, interp=4, tol_sdc=tol_c)
         out["cubic_mixed"] = run_variant(args, w, u0, uT, out, "mixed", 0.0, interp=4,
                                          tol_sdc=tol_c)
-        out["cubic_adaptive"] = run_variant(args, w, u0, uT, out, "fp64", ADAPTIVE_REL["fp64"],
-                                            interp=4, tol_sdc=tol_c)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fv = st["vcycles_level"][0] / max(args.steps, 1)

@@ -100,6 +100,15 @@ template <typename T>
 cudaError_t launch_update(const Grid& g, int B, const T* e, double* u64, long long u64_stride,
                           const int* active, cudaStream_t st);
 
+// Device-side stop rule of a multigrid solve after a residual: per item b that
+// is active, last[b] = its residual norm (from norm_bits); init: deactivate
+// items already at tol; else count the cycle (ncyc[b]++) and deactivate at
+// norm <= tol[b] or ncyc[b] >= *max_cycles (device memory, so that a captured
+// graph serves any cap).  A NaN/Inf norm deactivates the item and sets *nan_flag.
+cudaError_t launch_mg_check(int B, const unsigned long long* norm_bits, int* active,
+                            const double* tol, int* ncyc, double* last, const int* max_cycles,
+                            int* nan_flag, bool init, cudaStream_t st);
+
 // max|u| per item into norm_bits (bits of the double), FP64 input.
 cudaError_t launch_maxabs(const Grid& g, int B, const double* u, long long u_stride,
                           unsigned long long* norm_bits, const int* active, cudaStream_t st);

@@ -312,6 +312,32 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
   return cudaGetLastError();
 }
 
+__global__ void k_mg_check(int B, const unsigned long long* __restrict__ norm_bits, int* active,
+                           const double* __restrict__ tol, int* ncyc, double* last,
+                           const int* max_cycles, int* nan_flag, int init) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B || !active[b]) return;
+  const double n = __longlong_as_double((long long)norm_bits[b]);
+  last[b] = n;
+  if (!(n <= 1e300)) {
+    *nan_flag = 1;
+    active[b] = 0;
+    return;
+  }
+  if (!init) ncyc[b] += 1;
+  if (n <= tol[b] || (!init && ncyc[b] >= *max_cycles)) active[b] = 0;
+}
+
+cudaError_t launch_mg_check(int B, const unsigned long long* norm_bits, int* active,
+                            const double* tol, int* ncyc, double* last, const int* max_cycles,
+                            int* nan_flag, bool init, cudaStream_t st) {
+  if (B <= 0) return cudaSuccess;
+  k_mg_check<<<(B + 63) / 64, 64, 0, st>>>(B, norm_bits, active, tol, ncyc, last, max_cycles,
+                                           nan_flag, init ? 1 : 0);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prolong_add_cubic(const Grid& gc, const Grid& gf, int B, const double* ec,
                                      long long ec_stride, double* uf, long long uf_stride,
                                      cudaStream_t st) {

@@ -296,6 +296,10 @@ static size_t plan(heat3d_ctx* c, char* base) {
     L.coef64 = (Coef<double>*)take(sizeof(Coef<double>) * L.nslots * B);
     L.norms = (unsigned long long*)take(sizeof(unsigned long long) * B);
     L.active = (int*)take(sizeof(int) * B);
+    L.mg_tol_d = (double*)take(sizeof(double) * B);
+    L.mg_ncyc = (int*)take(sizeof(int) * B);
+    L.mg_last = (double*)take(sizeof(double) * B);
+    L.mg_flag = (int*)take(sizeof(int) * 2);  // NaN flag, cycle cap
   }
   c->map_d = (FasMap*)take(sizeof(FasMap));
   off = (off + 255) / 256 * 256;
@@ -617,7 +621,8 @@ static void graph_harvest(heat3d_ctx* c, CycleGraph* g) {
   c->prof_bytes += g->prof_bytes * c->work_scale;
   c->prof_dpops += g->prof_dpops * c->work_scale;
   c->prof_flops += g->prof_flops * c->work_scale;
-  c->prof_launches += g->prof_launches;
+  // launches that did work: a chunk's cycles after convergence skip every item
+  c->prof_launches += llround(g->prof_launches * c->work_scale);
 }
 
 // Captures fn() (the kernels of one cycle) into a new graph for this key.  The
@@ -691,6 +696,91 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
     return HEAT3D_OK;
   };
+  const int inner = std::max(1, c->cfg.mg.inner);
+  auto one_cycle = [&]() -> int {
+    T* cur = nullptr;
+    for (int q = 0; q < inner; ++q)
+      RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &cur, q > 0, q == inner - 1));
+    return residual();
+  };
+  if (graphs_usable(c)) {
+    // Chunked cycles: the stop rule runs on the device after every residual
+    // (launch_mg_check turns converged items off, so the kernels of later
+    // cycles skip them), and the host synchronises once per chunk of cycles:
+    // the same cycles as checking after each one.  Small grids take chunks
+    // of 4 (their cycles are short against a host round trip), large grids 1.
+    const int chunk = g.N >= 127 ? 1 : 4;
+    std::vector<double> tl(B);
+    for (int b = 0; b < B; ++b) tl[b] = fixed ? -1.0 : (tolv ? tolv[b] : tol);
+    const int hdr[2] = {0, max_cycles};
+    CK(cudaMemcpyAsync(L.mg_tol_d + b0, tl.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(L.mg_flag, hdr, sizeof(hdr), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(L.mg_ncyc + b0, 0, sizeof(int) * B, st));
+    RET(residual());
+    CK(launch_mg_check(B, L.norms + b0, act, L.mg_tol_d + b0, L.mg_ncyc + b0, L.mg_last + b0,
+                       L.mg_flag + 1, L.mg_flag, true, st));
+    auto chunk_fn = [&]() -> int {
+      for (int q = 0; q < chunk; ++q) {
+        RET(one_cycle());
+        CK(launch_mg_check(B, L.norms + b0, act, L.mg_tol_d + b0, L.mg_ncyc + b0, L.mg_last + b0,
+                           L.mg_flag + 1, L.mg_flag, false, st));
+      }
+      return HEAT3D_OK;
+    };
+    CycleGraph* gph = find_graph(c, lev, slot, b0, B, u, rhs);
+    if (gph && gph->prof_class != c->prof_class) {
+      drop_graph(c, gph);
+      gph = nullptr;
+    }
+    if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, chunk_fn, &gph));
+    std::vector<int> hact(B), hcyc(B, 0), prev(B, 0);
+    int launched = 0;
+    for (;;) {
+      CK(cudaGraphLaunch(gph->exec, st));
+      h3d::launches_adjust(gph->launches);
+      launched += chunk;
+      CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(hcyc.data(), L.mg_ncyc + b0, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      long long done = 0;
+      for (int b = 0; b < B; ++b) done += hcyc[b] - prev[b];
+      prev = hcyc;
+      // work of this replay: item-cycles done out of chunk * B launched
+      c->work_scale = (double)done / ((double)chunk * B);
+      c->bytes += gph->bytes * c->work_scale;
+      if (!gph->ev.empty()) graph_harvest(c, gph);
+      c->work_scale = 1.0;
+      bool any = false;
+      for (int b = 0; b < B; ++b) any = any || hact[b];
+      if (!any || launched >= max_cycles) break;
+    }
+    std::vector<double> last(B);
+    int hflag[2];
+    CK(cudaMemcpyAsync(last.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hflag, L.mg_flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hflag[0]) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
+    long long total = 0;
+    double mx = 0;
+    int notconv = 0;
+    for (int b = 0; b < B; ++b) {
+      total += hcyc[b];
+      mx = std::max(mx, last[b]);
+      if (!fixed && !(last[b] <= tl[b])) ++notconv;
+    }
+    if (s) {
+      s->vcycles += total * inner;
+      s->vcycles_level[lev] += total * inner;
+      s->solves += B;
+      s->mg_residual = mx;
+    }
+    if (notconv > 0) {
+      if (s) s->notconv += notconv;
+      return h3d_fail(c, HEAT3D_ENOTCONV, "multigrid: %d item(s) above tol %.3g after %d cycles",
+                      notconv, tol, max_cycles);
+    }
+    return HEAT3D_OK;
+  }
   RET(residual());
   int cycles = 0, live = B;
   if (!fixed) {
@@ -701,38 +791,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     }
     if (live < B) CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
   }
-  const int inner = std::max(1, c->cfg.mg.inner);
-  auto one_cycle = [&]() -> int {
-    T* cur = nullptr;
-    for (int q = 0; q < inner; ++q)
-      RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &cur, q > 0, q == inner - 1));
-    return residual();
-  };
-  CycleGraph* gph = nullptr;
-  if (graphs_usable(c)) {
-    gph = find_graph(c, lev, slot, b0, B, u, rhs);
-    if (gph && gph->prof_class != c->prof_class) {
-      drop_graph(c, gph);
-      gph = nullptr;
-    }
-    if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, one_cycle, &gph));
-  }
   while (cycles < max_cycles && live > 0) {
     c->work_scale = (double)live / B;  // converged items skip their blocks
-    if (gph) {
-      CK(cudaGraphLaunch(gph->exec, st));
-      h3d::launches_adjust(gph->launches);
-      c->bytes += gph->bytes * c->work_scale;
-      if (!gph->ev.empty()) {
-        CK(cudaStreamSynchronize(st));
-        graph_harvest(c, gph);
-      }
-    } else {
-      int rc = one_cycle();
-      if (rc < 0) c->work_scale = 1.0;
-      RET(rc);
-    }
+    int rc = one_cycle();
     c->work_scale = 1.0;
+    RET(rc);
     ++cycles;
     if (s) {
       s->vcycles += (long long)live * inner;

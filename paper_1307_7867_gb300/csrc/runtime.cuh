@@ -44,6 +44,12 @@ struct SdcLevel {
   Coef<double>* coef64 = nullptr;  // Coef<double>[slot][item], finest multigrid level
   unsigned long long* norms = nullptr;
   int* active = nullptr;
+  // device-side stop rule of the multigrid solves (chunked cycles): per-item
+  // tolerance, cycles done and last residual norm; a NaN flag
+  double* mg_tol_d = nullptr;
+  int* mg_ncyc = nullptr;
+  double* mg_last = nullptr;
+  int* mg_flag = nullptr;
   // host mirrors
   std::vector<ItemSDC> items_h;
   std::vector<double> t0, nu, dt;

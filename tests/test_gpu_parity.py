@@ -363,6 +363,41 @@ def test_every_launch_shape_is_bitwise_identical(H, oracle, precision, monkeypat
     monkeypatch.delenv("HEAT3D_SHAPE")
 
 
+def test_chunked_device_stop_rule_matches_host_loop(H, oracle):
+    """With graphs the stop rule runs on the device and the host waits once per
+    chunk of cycles (4 on grids below 127): identical cycles and results to
+    the host-checked loop, for tolerance, fixed-count and cycle-cap solves and
+    for MLSDC with several items (PFASST slices)."""
+    N, c = 31, 0.01
+    b = inputs.random_field(N, seed=21)
+    outs = {}
+    for graphs in (0, 1):
+        ctx = H.Context(H.make_config((N, 4, 3), use_graphs=graphs), stream=torch.cuda.Stream())
+        u = dev(np.zeros_like(b))
+        rc, st = H.mg_vcycle(ctx, 0, c, dev(b), u, 50, 1e-12)
+        uf = dev(np.zeros_like(b))
+        H.mg_vcycle(ctx, 0, c, dev(b), uf, 3, -1.0)
+        un = dev(np.zeros_like(b))
+        rcn, stn = H.mg_vcycle(ctx, 0, c, dev(b), un, 2, 1e-14, allow_notconv=True)
+        outs[graphs] = (host(u), st["vcycles"], host(uf), rcn, stn["notconv"], host(un))
+    g0, g1 = outs[0], outs[1]
+    assert np.array_equal(g0[0], g1[0]) and g0[1] == g1[1]
+    assert np.array_equal(g0[2], g1[2]) and np.array_equal(g0[5], g1[5])
+    assert g1[3] == H.ENOTCONV and g1[4] == 1
+    ref, _, ocyc, _ = oracle.mg_solve(np.zeros_like(b), b, 4, c, tol=1e-12, max_cycles=50)
+    assert g1[1] == ocyc
+    res = []
+    for graphs in (0, 1):
+        cfg = H.make_config((31, 4, 5), (15, 2, 3), dt=1 / 16, T=4 / 16, sweeps_fine=1, slices=4,
+                            iters=3, tol_sdc=-1.0, mg_tol=1e-11, use_graphs=graphs)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.smooth_random_field(31, seed=22, kmax=4)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        res.append((uT, st["vcycles"]))
+    assert np.array_equal(res[0][0], res[1][0]) and res[0][1] == res[1][1]
+
+
 def test_graph_replay_counts_launches_and_profile(H):
     """Launch counter and the kernel profile include graph replays."""
     N = 63
