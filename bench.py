@@ -40,6 +40,15 @@ import numpy as np  # noqa: E402
 REF_FINE_VCYCLES_PER_STEP = 596.0
 REF_COARSE_VCYCLES_PER_STEP = 164.0
 
+# DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
+# capture of the kernel as it is now (profiles/stencils_fine_255_*.md); key:
+# (precision, fine stencil order, N).  Must be cleared when that kernel changes.
+TRAFFIC_BYTES = {
+    ("fp64", 4, 255): 378.9e6,   # k_tile OpJacobi<double, 4>, fine level
+    ("fp64", 19, 255): 376.4e6,  # k_tile OpJacobi<double, 19>, fine level
+    ("mixed", 4, 255): 378.1e6,  # k_tile OpResid64<4, float>, fine level
+}
+
 WORKLOADS = {
     "c2": dict(
         desc="two-level MLSDC, fine 255^3 wide M=5 / coarse 127^3 7-point M=3, dt=1/64, "
@@ -290,7 +299,8 @@ def run_ours(args, w, rank, world):
                     "hbm_frac_of_measured": round(prof["bytes"] / prof["launches"] / per_launch_s / 1e9
                                                   / pk["hbm_gbs"], 4),
                     "launches": prof["launches"], "avg_launch_us": round(per_launch_s * 1e6, 2),
-                    "traffic": None}
+                    "traffic": TRAFFIC_BYTES.get((w["precision"], w["fine"][1], Nf)),
+                    "traffic_unit": "bytes per launch (ncu dram read + write)"}
         else:
             gbs = prof["bytes"] / prof["launches"] / per_launch_s / 1e9
             roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": pk["hbm_gbs"], "unit": "GB/s",
