@@ -618,6 +618,9 @@ def main():
                     help="skip the mixed-precision and adaptive-tolerance variants")
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"],
                     help="override the workload's precision")
+    ap.add_argument("--sweeps-fine", type=int, default=None,
+                    help="override the fine sweeps per iteration")
+    ap.add_argument("--iters", type=int, default=None, help="override the iteration cap")
     ap.add_argument("--interp", type=int, default=None, choices=[2, 4],
                     help="interpolation of the coarse correction: 2 trilinear, 4 cubic")
     ap.add_argument("--mg-rel", type=float, default=None,
@@ -643,6 +646,11 @@ def main():
                  desc=w["desc"] + f"; solves stop at max(mg_tol, {args.mg_rel} x sweep residual)")
     if args.interp == 4:
         w = dict(w, interp=4, desc=w["desc"] + "; cubic interpolation of the coarse correction")
+    if args.sweeps_fine:
+        w = dict(w, sweeps_fine=args.sweeps_fine,
+                 desc=w["desc"] + f"; {args.sweeps_fine} fine sweeps per iteration")
+    if args.iters:
+        w = dict(w, iters=args.iters, desc=w["desc"] + f"; at most {args.iters} iterations")
     if args.precision and args.precision != w["precision"]:
         w = dict(w, precision=args.precision,
                  desc=w["desc"] + ("; FP32 V-cycles in FP64 refinement" if args.precision == "mixed"

@@ -106,8 +106,11 @@ typedef struct {
                                The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-14,
                                planes per block zc) forces one shape on every stencil of
                                grids with N >= 16 instead (testing) */
-  int fuse_coarse;          /* 1: run the multigrid levels with N <= 15 of a V-cycle in one
-                               kernel, all levels in shared memory (results identical) */
+  int fuse_coarse;          /* 1: run the coarse multigrid levels of a V-cycle in one kernel,
+                               all levels in shared memory (results identical): the levels
+                               with N <= 15, or N <= 7 or 3 when the autotuner times that
+                               faster (the environment variable HEAT3D_FUSE_MAX=n forces n,
+                               for testing) */
   int interp;               /* spatial interpolation of the coarse correction in the FAS
                                step (Sec. 1.1; the paper does not say which): 2 trilinear
                                (default), 4 tensor-product cubic (4-point midpoint rule,

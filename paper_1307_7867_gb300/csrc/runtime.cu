@@ -485,7 +485,8 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   T* t = mgbuf<T>(L, k, 2, b0);
   const Coef<T>* cf = coefT<T>(L, slot, k, b0);
   const size_t ts = sizeof(T), pts = (size_t)g.N * g.N * g.N * B;
-  if (k > 0 && c->cfg.fuse_coarse && g.N <= kFusedMaxN && L.L.order != kCompact) {
+  if (k > 0 && c->cfg.fuse_coarse && g.N <= std::min(L.fuse_max, kFusedMaxN) &&
+      L.L.order != kCompact) {
     // this level and every coarser one in a single kernel (same arithmetic)
     int Ns[kMaxLevels];
     const Coef<T>* cfs[kMaxLevels];
@@ -1227,6 +1228,30 @@ static int autotune_T(heat3d_ctx* c, cudaEvent_t e0, cudaEvent_t e1) {
       if (ms < best) { best = ms; pick = sh; }
     }
     L.shape64 = pick;
+    // How far down to fuse the coarse levels: the fused kernel runs on one SM
+    // per item, so deep fusion saves launches but can cost FP64 throughput.
+    // Time the V-cycle below the first level with N <= 15 for each choice.
+    int k15 = -1;
+    for (int k = 1; k < L.nmg; ++k)
+      if (L.mg[k].N <= kFusedMaxN) { k15 = k; break; }
+    if (c->cfg.fuse_coarse && L.L.order != kCompact && k15 > 0) {
+      float bestf = 1e30f;
+      int pickf = kFusedMaxN;
+      for (int fm : {15, 7, 3, 0}) {
+        L.fuse_max = fm;
+        float ms = time_shape(c, e0, e1, [&] {
+          T* cur = nullptr;
+          return vcycle_level<T>(c, L, 0, k15, 0, L.B, nullptr, nullptr, 0, &cur) == HEAT3D_OK
+                     ? cudaSuccess
+                     : cudaErrorUnknown;
+        });
+        if (tune_log())
+          fprintf(stderr, "tune fuse T%zu order %d below N %d: fuse_max %d: %.4f ms\n", sizeof(T),
+                  L.L.order, L.mg[k15].N, fm, ms);
+        if (ms < bestf) { bestf = ms; pickf = fm; }
+      }
+      L.fuse_max = pickf;
+    }
   }
   return HEAT3D_OK;
 }
@@ -1369,6 +1394,12 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   CK(cudaStreamSynchronize(c->st));
   c->bound = true;
   if (c->cfg.autotune) RET(h3d_autotune(c));
+  // HEAT3D_FUSE_MAX=n forces the coarse-level fusion depth (testing)
+  if (const char* f = getenv("HEAT3D_FUSE_MAX")) {
+    int fm = -1;
+    if (sscanf(f, "%d", &fm) == 1 && fm >= 0)
+      for (int l = 0; l < c->cfg.nlevels; ++l) c->lv[l].fuse_max = fm;
+  }
   // HEAT3D_SHAPE=kind,zc forces one launch shape on every stencil (testing:
   // every shape must give bitwise the same results)
   if (const char* f = getenv("HEAT3D_SHAPE")) {

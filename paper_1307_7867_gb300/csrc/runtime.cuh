@@ -58,6 +58,9 @@ struct SdcLevel {
   // the FP64 kernels (operator, refinement residual) on the level's grid
   Shape shapeT[kMaxLevels];
   Shape shape64;
+  // multigrid levels with N <= fuse_max run as one fused kernel per V-cycle
+  // (when fuse_coarse is on); chosen by the autotuner among 15, 7, 3 and 0
+  int fuse_max = 15;
 };
 
 // A captured V-cycle (+ norm reset + refinement residual) for one solve key.

@@ -363,6 +363,26 @@ def test_every_launch_shape_is_bitwise_identical(H, oracle, precision, monkeypat
     monkeypatch.delenv("HEAT3D_SHAPE")
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_every_fusion_depth_is_bitwise_identical(H, precision, monkeypatch):
+    """The coarse levels fused into one kernel down from N <= 15, 7, 3 or not
+    at all give bitwise the same MLSDC result and V-cycles."""
+    prec = H.FP64 if precision == "fp64" else H.MIXED
+    outs = []
+    for fm in (15, 7, 3, 0):
+        monkeypatch.setenv("HEAT3D_FUSE_MAX", str(fm))
+        cfg = H.make_config((63, 4, 5), (31, 2, 3), dt=1 / 32, T=2 / 32, precision=prec,
+                            mg_tol=1e-11, use_graphs=1, inner=2 if prec == H.MIXED else 1)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.smooth_random_field(63, seed=23, kmax=5)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        outs.append((uT, st["vcycles"]))
+    monkeypatch.delenv("HEAT3D_FUSE_MAX")
+    for uT, v in outs[1:]:
+        assert np.array_equal(uT, outs[0][0]) and v == outs[0][1]
+
+
 def test_chunked_device_stop_rule_matches_host_loop(H, oracle):
     """With graphs the stop rule runs on the device and the host waits once per
     chunk of cycles (4 on grids below 127): identical cycles and results to
