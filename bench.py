@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -125,7 +126,8 @@ class ClockSampler:
     def __init__(self, gpu):
         self.gpu = gpu
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.environ.get("HEAT3D_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"heat3d_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -406,7 +408,7 @@ def cpu_baseline(w, fine_v, coarse_v, sample_desc_extra=""):
 
 
 def run_reference(args, w):
-    """The oracle on the machine's host cores: each step is one fine V-cycle at full size,
+    """The oracle on this machine's host cores: each step is one fine V-cycle at full size,
     scaled to grid-pt-steps/s by the V-cycles one step of this workload performs."""
     from oracle import oracle as O
     O.build()
