@@ -183,6 +183,14 @@ def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None, interp
                          interp=w.get("interp", 2) if interp is None else interp)
 
 
+def workload_config(w, world):
+    """The JSON line's config: the workload and the options it runs with."""
+    return {"workload": w["desc"], "N_fine": w["fine"][0], "dt": w["dt"],
+            "mg_rel": w.get("mg_rel", 0.0), "interp": w.get("interp", 2),
+            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "working set >> L2 (fields of 133 MB+), no flush needed"}
+
+
 def max_over_ranks(seconds, device, world):
     """Slowest rank's time (MAX all-reduce); the value of a single rank alone."""
     if world <= 1:
@@ -317,10 +325,7 @@ def run_ours(args, w, rank, world):
         "ms_per_step": secs * 1e3 / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if w["precision"] == "fp64" else "f64+f32",
         "data": "synthetic (analytic initial value and forcing, Eqs. 3-4)",
-        "config": {"workload": w["desc"], "N_fine": Nf, "dt": dt, "mg_rel": w.get("mg_rel", 0.0),
-                   "interp": w.get("interp", 2),
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "working set >> L2 (fields of 133 MB+), no flush needed"},
+        "config": workload_config(w, world),
         "stats": {k: st[k] for k in ("vcycles", "vcycles_level", "solves", "sweeps", "iters",
                                      "notconv", "residual")},
         "accuracy": {"rel_err_vs_pde_solution": err_pde, "rel_err_vs_semidiscrete": err_sd,
@@ -425,7 +430,7 @@ def run_reference(args, w):
             "unit": "grid-pt-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["desc"]},
+            "config": workload_config(w, 1),
             "cpu_baseline": {"value": v, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle",
                              "sample": "per step: one fine V(2,1) cycle of the oracle at full size, "
                                        f"scaled by {REF_FINE_VCYCLES_PER_STEP:.0f} fine + "
