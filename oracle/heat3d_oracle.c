@@ -19,7 +19,7 @@
  *     19-point Mehrstellen operator (order 19, Sec. 1 and Sec. 1.2): the
  *     semi-discrete system is W u' = nu L u + W f with the weighting matrix
  *     W = I + (h^2/12) Delta_7; SDC runs in that weighted form and the FAS
- *     restriction applies W^{-1} (by multigrid) to the fine integrals;
+ *     restriction maps the fine integrals back by W^{-1} (multigrid);
  *   - M counts Gauss-Lobatto nodes including both ends of the step;
  *   - multigrid: damped Jacobi (omega 6/7 for 7 points, 9/11 for 13 points,
  *     12/11 for the compact operator, constant interior diagonal),
@@ -28,8 +28,12 @@
  *     unknown solved exactly (Sec. 1.2);
  *   - solve stop rule: max|b - A u| <= tol, checked before every cycle;
  *   - SDC initial iterate: the initial value spread to every node;
- *   - FAS: injection in space and time, trilinear + Lagrange interpolation of
- *     the coarse correction; PFASST schedule and predictor as coded below.
+ *   - FAS: injection in space and time, trilinear (or, with interp = 4,
+ *     tensor-product cubic) + Lagrange interpolation of the coarse
+ *     correction; PFASST schedule and predictor as coded below;
+ *   - optional solver tolerance tied to the sweep's incoming residual
+ *     (mg_rel), and the W-solve of the compact FAS restriction applied to the
+ *     weighted residual (U_j - U_0 + W^{-1} r), see or_fas_restrict_st.
  */
 #include <math.h>
 #include <stdlib.h>
