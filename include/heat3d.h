@@ -105,7 +105,9 @@ typedef struct {
                                heat3d_bind_workspace and keep the fastest (results identical).
                                The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-14,
                                planes per block zc) forces one shape on every stencil of
-                               grids with N >= 16 instead (testing) */
+                               grids with N >= 16 instead (testing); HEAT3D_TUNE_FILE=path
+                               reuses the shapes recorded in that file for levels it lists
+                               and appends the timed choices of the others */
   int fuse_coarse;          /* 1: run the coarse multigrid levels of a V-cycle in one kernel,
                                all levels in shared memory (results identical): the levels
                                with N <= 15, or N <= 7 or 3 when the autotuner times that

@@ -383,6 +383,28 @@ def test_every_fusion_depth_is_bitwise_identical(H, precision, monkeypatch):
         assert np.array_equal(uT, outs[0][0]) and v == outs[0][1]
 
 
+def test_tune_file_records_and_reuses_shapes(H, monkeypatch, tmp_path):
+    """HEAT3D_TUNE_FILE: the first context times its shapes and records one
+    line per SDC level; a second context takes them from the file (no timing)
+    and gives bitwise the same result."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("HEAT3D_TUNE_FILE", str(path))
+    outs = []
+    for _ in range(2):
+        cfg = H.make_config((63, 4, 5), (31, 2, 3), dt=1 / 32, T=2 / 32, mg_tol=1e-11, use_graphs=1)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.smooth_random_field(63, seed=24, kmax=5)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        outs.append((uT, st["vcycles"]))
+        ctx.close()
+    lines = path.read_text().strip().splitlines()
+    assert len(lines) == 2  # one per level, written once
+    assert [int(x) for x in lines[0].split()[:4]] == [8, 4, 63, 1]
+    assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+    monkeypatch.delenv("HEAT3D_TUNE_FILE")
+
+
 def test_chunked_device_stop_rule_matches_host_loop(H, oracle):
     """With graphs the stop rule runs on the device and the host waits once per
     chunk of cycles (4 on grids below 127): identical cycles and results to
