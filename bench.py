@@ -556,6 +556,7 @@ def run_alpha(args):
     from paper_1307_7867_gb300 import build, heat3d as H, inputs
     build.build()
     fine, coarse, dt = (127, 4, 5), (63, 2, 3), 1 / 16
+    interp = args.interp or 2
     u0 = inputs.sine_mode(127)
     st_ = torch.cuda.Stream()
 
@@ -563,7 +564,7 @@ def run_alpha(args):
         cfg = H.make_config(fine, coarse if nlevels == 2 else None, dt=dt, T=P * dt,
                             sweeps_fine=sweeps, sweeps_coarse=1, slices=P if nlevels == 2 else 1,
                             iters=50, tol_sdc=1e-10, mg_tol=1e-11, batch=max(P, 1),
-                            use_graphs=1, autotune=1)
+                            use_graphs=1, autotune=1, interp=interp)
         return H.Context(cfg, stream=st_)
 
     # alpha and beta from single-slice sweeps on a representative state
@@ -603,7 +604,8 @@ def run_alpha(args):
                      "speedup_measured": measured, "residual": sp["residual"]})
         cp.close()
     return {"workload": "speedup model (Eq. pfasst_speedup) on one GB300: fine 127^3 wide M=5, "
-                        "coarse 63^3 7-point M=3, dt=1/16, residual 1e-10",
+                        "coarse 63^3 7-point M=3, dt=1/16, residual 1e-10"
+                        + ("; cubic interpolation of the coarse correction" if interp == 4 else ""),
             "alpha": alpha, "beta": beta, "K_S": K_S, "t_fine_sweep_s": t_f,
             "t_coarse_sweep_s": t_c, "t_fas_s": t_r, "t_serial_sdc_16_steps_s": t_serial16,
             "pfasst": rows,
