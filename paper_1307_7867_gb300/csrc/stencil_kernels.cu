@@ -562,8 +562,10 @@ cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active
 // points of one row, so every neighbour read is a 16-byte (centre, y, z) or
 // 8-byte (x halo) shared-memory access shared by four points, and the
 // per-point loads and stores are float4.  Ring and loader as k_tile (the
-// 16-byte x halo is exactly one chunk).  The sums per point are formed in the
-// same order as k_tile and k_zmarch, so the results are bitwise identical.
+// 16-byte x halo is exactly one chunk); the boundary cells of the x and y
+// halo are written into the ring instead of being fixed per point.  The sums
+// per point are formed in the same order as k_tile and k_zmarch, so the
+// results are bitwise identical.
 template <int ORDER, int TYT, int RY, int D>
 constexpr int tile4_smem() {
   return (2 * (ORDER == 4 ? 2 : 1) + D + 1) * (TYT * RY + 2 * (ORDER == 4 ? 2 : 1)) * (128 + 8) * 4;
@@ -633,7 +635,44 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
   const int jb = y0 + ty * RY;
   const int sbase = (R + ty * RY) * SX + XH + 4 * tx;
   const int nx = N - i;  // points of the thread's four inside the grid
-  const bool xedge = i == 0 || nx <= 5;  // a[] holds a cell outside the domain
+  // Boundary cells of a plane held in the ring (x and y out of the domain)
+  // are written with the boundary rule once the plane has arrived, so the
+  // stencil reads them like any neighbour: indices -1 and N are 0, the wide
+  // stencil's ghosts -2 and N+1 minus the cell at 0 and N-1.  Corners (out in
+  // x and y) are never read by these axis-aligned stencils.
+  const int cxN = XH + N - x0;  // ring column of x = N
+  const bool xlo = x0 == 0, xhi = cxN < SX;
+  const int ryN = N - (y0 - R);  // ring row of y = N
+  const bool ylo = y0 < R, yhi = ryN < SY;
+  auto fill = [&](int z, int slot) {
+    if (z < 0 || z >= N || !(xlo || xhi || ylo || yhi)) return;
+    float* P = ring + slot * PS;
+    if (xlo || xhi)
+      for (int r = tid; r < SY; r += NT) {
+        const int y = y0 - R + r;
+        if (y < 0 || y >= N) continue;
+        float* row = P + r * SX;
+        if (xlo) {
+          if (R == 2) row[XH - 2] = -row[XH];
+          row[XH - 1] = 0.f;
+        }
+        if (xhi) {
+          if (R == 2 && cxN + 1 < SX) row[cxN + 1] = -row[cxN - 1];
+          row[cxN] = 0.f;
+        }
+      }
+    if (ylo || yhi)
+      for (int c = tid; c < SX; c += NT) {
+        if (ylo) {  // rows y = -1 and -2 sit at ring rows R - 1 and R - 2
+          if (R == 2) P[c] = -P[R * SX + c];
+          P[(R - 1) * SX + c] = 0.f;
+        }
+        if (yhi) {
+          if (R == 2 && ryN + 1 < SY) P[(ryN + 1) * SX + c] = -P[(ryN - 1) * SX + c];
+          P[ryN * SX + c] = 0.f;
+        }
+      }
+  };
   int idx0 = z0 * plane + jb * g.px + i;
   int cs = R;
   int fs_ = 2 * R + D;
@@ -644,6 +683,19 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
       if (nx > 0 && jb + r < N) ex[r] = o.load4(idx0 + r * g.px);
     cp_async_wait<D - 1>();
     __syncthreads();
+    // planes up to k + R have arrived: complete the boundary cells of plane
+    // k + R (read as a centre plane R iterations later, after a barrier); the
+    // first iteration also completes planes k .. k + R - 1 and waits for that
+    if (k == z0) {
+      int sl = cs;
+      for (int q = 0; q < R; ++q, sl = ring_next(sl, NB)) fill(k + q, sl);
+      fill(k + R, sl);
+      __syncthreads();
+    } else {
+      int sl = cs;
+      for (int q = 0; q < R; ++q) sl = ring_next(sl, NB);
+      fill(k + R, sl);
+    }
     issue(k + R + D, fs_);
     fs_ = ring_next(fs_, NB);
     const int sm1 = ring_prev(cs, NB), sp1 = ring_next(cs, NB);
@@ -674,22 +726,6 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
         a[2] = 0.f; a[3] = P0[o0 - 1]; a[8] = P0[o0 + 4]; a[9] = 0.f;
       }
       a[4] = c[0]; a[5] = c[1]; a[6] = c[2]; a[7] = c[3];
-      // x boundary rule on the ten x values (a[m] sits at x = i + m - 4): the
-      // cells -1 and N read 0, the ghosts -2 and N+1 minus u(0) and u(N-1)
-      if (xedge) {
-        if (i == 0) {
-          a[3] = 0.f;
-          a[2] = -a[4];
-        }
-        switch (nx) {
-          case 1: a[5] = 0.f; a[6] = R == 2 ? -a[4] : a[6]; break;
-          case 2: a[6] = 0.f; a[7] = R == 2 ? -a[5] : a[7]; break;
-          case 3: a[7] = 0.f; a[8] = R == 2 ? -a[6] : a[8]; break;
-          case 4: a[8] = 0.f; a[9] = R == 2 ? -a[7] : a[9]; break;
-          case 5: a[9] = 0.f; break;
-          default: break;
-        }
-      }
       const float4 ym1 = col[r + R - 1], yp1 = col[r + R + 1];
       const float4 zm1 = *reinterpret_cast<const float4*>(Pm1 + o0);
       const float4 zp1 = *reinterpret_cast<const float4*>(Pp1 + o0);
@@ -716,10 +752,6 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
           xm2v[q] = a[2 + q];
           xp2v[q] = a[6 + q];
         }
-      }
-      if (j < R || j >= N - R) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) fix_axis<float, R>(j, N, c[q], ym1v[q], yp1v[q], ym2v[q], yp2v[q]);
       }
       if (zedge) {
 #pragma unroll
