@@ -626,7 +626,7 @@ static void graph_harvest(heat3d_ctx* c, CycleGraph* g) {
   c->prof_launches += llround(g->prof_launches * c->work_scale);
 }
 
-// Captures fn() (the kernels of one cycle) into a new graph for this key.  The
+// Captures fn() (the kernels of one chunk of cycles) into a new graph for this key.  The
 // launches and bytes it enqueues are recorded per replay instead of now.
 template <typename Fn>
 static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* u,

@@ -63,7 +63,8 @@ struct SdcLevel {
   int fuse_max = 15;
 };
 
-// A captured V-cycle (+ norm reset + refinement residual) for one solve key.
+// A captured chunk of solve cycles (each: V-cycle(s), norm reset, refinement
+// residual, device-side stop rule) for one solve key.
 struct CycleGraph {
   int lev = 0, slot = 0, b0 = 0, B = 0;
   const double* u = nullptr;
