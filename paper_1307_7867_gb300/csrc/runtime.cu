@@ -1019,7 +1019,18 @@ int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
   if (F.L.N == G.L.N) {
     CK(launch_update<double>(F.g, B * MF, D, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
   } else if (c->cfg.interp == 4) {
-    CK(launch_prolong_add_cubic(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
+    if (MF >= 3) {
+      // separable passes node by node, temporaries in the fine integral
+      // fields I (free between sweeps): fields 0 and 1 of each item
+      const long long is = (long long)(MF - 1) * ff;
+      double* I0 = F.I + (size_t)b0 * (MF - 1) * ff;
+      for (int j = 0; j < MF; ++j)
+        CK(launch_prolong_add_cubic(G.g, F.g, B, D + (size_t)j * gf, (long long)MF * gf,
+                                    F.U + (size_t)b0 * MF * ff + (size_t)j * ff, (long long)MF * ff,
+                                    st, I0, I0 + ff, is));
+    } else {
+      CK(launch_prolong_add_cubic(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
+    }
   } else {
     CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
   }
