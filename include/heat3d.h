@@ -99,8 +99,11 @@ typedef struct {
   int batch;                /* state slots per level for sdc_sweep / serving (>= slices) */
   int device;               /* CUDA device ordinal */
   void* stream;             /* cudaStream_t for all work of this context (NULL: legacy) */
-  int use_graphs;           /* 1: replay each V-cycle from a captured CUDA graph (needs a
-                               non-default stream; ignored on the legacy stream) */
+  int use_graphs;           /* 1: replay the solve cycles from captured CUDA graphs, with the
+                               stop rule on the device and one host wait per chunk of cycles
+                               (4 on grids below 127, else 1); same cycles and results as
+                               without (needs a non-default stream; ignored on the legacy
+                               stream) */
   int autotune;             /* 1: time the stencil launch shapes of every multigrid level at
                                heat3d_bind_workspace and keep the fastest (results identical).
                                The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-14,
