@@ -113,3 +113,29 @@ def test_fullsize_511_mixed_step(H):
     assert st["residual"] <= 1e-10 and st["notconv"] == 0
     err, impurity = _mode_error(uT.cpu().numpy(), 1 / 32, -3 * NU * np.pi**2)
     assert err <= 1e-10 and impurity <= 1e-9
+
+
+@pytest.mark.parametrize("order", [4, 19])
+def test_max_size_operator_on_sine_modes(H, order):
+    """The largest grid the library accepts (N = 1023, 1.07e9 points, 8.6 GB
+    per field): the operator applied to sine modes equals the mode times its
+    closed-form symbol, to the rounding of the stencil sums (fields made and
+    compared on the device)."""
+    N = 1023
+    ctx = H.Context(H.make_config((N, order, 2), nu=1.0, autotune=0))
+    h = 1.0 / (N + 1)
+    x = torch.arange(1, N + 1, device="cuda", dtype=torch.float64) * h
+    out = torch.empty(N, N, N, dtype=torch.float64, device="cuda")
+    for k in ((1, 1, 1), (3, 5, 7)):
+        sx, sy, sz = (torch.sin(kk * np.pi * x) for kk in k)
+        u = sz[:, None, None] * sy[None, :, None] * sx[None, None, :]
+        H.heat3d_apply_laplacian(ctx, 0, u, out)
+        if order == 4:
+            lam = sum(ind.eig_1d(N, 4, kk) for kk in k)
+        else:
+            lam = ind.compact_eigs(N, k)[0]
+        err = (out - lam * u).abs().max().item()
+        # rounding of the neighbour sums: coefficients up to ~8 / h^2
+        assert err <= 50 * 1e-14 / h**2, (k, err, lam)
+        del u
+    torch.cuda.synchronize()
