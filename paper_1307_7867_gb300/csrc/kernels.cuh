@@ -13,7 +13,7 @@ namespace h3d {
 // per thread), 2 shared-memory tile 32 x 8 (128 threads, 2 rows each), 3 tile
 // 32 x 16 (256 threads, 2 rows each), 4 tile 32 x 16 (128 threads, 4 rows
 // each), 5 and 6 as 2 and 3 with 6 planes of prefetch instead of 3; FP32
-// Jacobi and residual only: four x points per thread, tile 128 x TY: 7 (4
+// Jacobi and residual only (all three stencils): four x points per thread, tile 128 x TY: 7 (4
 // warps x 2 rows), 8 (8 warps x 1 row), 9 (4 warps x 4 rows), 10 (8 warps x
 // 2 rows), 11 and 12 as 7 and 8 with 6 planes of prefetch, 13 as 7 with 10,
 // 14 (2 warps x 2 rows, 6 planes); other operators take kind 3 for these; zc:

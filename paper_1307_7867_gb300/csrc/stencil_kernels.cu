@@ -243,8 +243,9 @@ struct OpJacobi {
   // Four consecutive x points (FP32 storage, k_tile4): idx is a multiple of
   // 4, n >= 1 of the four are inside the grid.  Same arithmetic per point as
   // apply().
-  static constexpr bool kVec4 = sizeof(TT) == 4 && ORDER != kCompact;
-  static constexpr int kRegFloor = UPD ? 96 : 64;  // registers k_tile4 keeps without spilling
+  static constexpr bool kVec4 = sizeof(TT) == 4;
+  // registers k_tile4 keeps without spilling
+  static constexpr int kRegFloor = ORDER == kCompact ? 128 : UPD ? 96 : 64;
   struct Ex4 { float4 r; double2 u01, u23; };
   __device__ Ex4 load4(int idx) const {
     Ex4 x;
@@ -261,8 +262,7 @@ struct OpJacobi {
     float v[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      float S = combine<float, ORDER>(s1[q], s2[q]);
-      float res = fmaf(-d, c[q], fmaf(ec, S, rr[q]));
+      float res = a_res<float, ORDER>(d, ec, e2c, c[q], s1[q], s2[q], rr[q]);
       v[q] = fmaf(wd, res, c[q]);
     }
     if (UPD) {
@@ -310,8 +310,8 @@ struct OpResid {
     o_[idx] = a_res<T, ORDER>(d, ec, e2c, c, s1, s2, ex.r);
     return 0.0;
   }
-  static constexpr bool kVec4 = sizeof(TT) == 4 && ORDER != kCompact;
-  static constexpr int kRegFloor = 64;
+  static constexpr bool kVec4 = sizeof(TT) == 4;
+  static constexpr int kRegFloor = ORDER == kCompact ? 128 : 64;
   struct Ex4 { float4 r; };
   __device__ Ex4 load4(int idx) const { return Ex4{*reinterpret_cast<const float4*>(r_ + idx)}; }
   __device__ void apply4(int idx, int n, const float (&c)[4], const float (&s1)[4],
@@ -319,10 +319,7 @@ struct OpResid {
     const float rr[4] = {ex.r.x, ex.r.y, ex.r.z, ex.r.w};
     float v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float S = combine<float, ORDER>(s1[q], s2[q]);
-      v[q] = fmaf(-d, c[q], fmaf(ec, S, rr[q]));
-    }
+    for (int q = 0; q < 4; ++q) v[q] = a_res<float, ORDER>(d, ec, e2c, c[q], s1[q], s2[q], rr[q]);
     if (n >= 4) {
       *reinterpret_cast<float4*>(o_ + idx) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
@@ -685,16 +682,17 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
     __syncthreads();
     // planes up to k + R have arrived: complete the boundary cells of plane
     // k + R (read as a centre plane R iterations later, after a barrier); the
-    // first iteration also completes planes k .. k + R - 1 and waits for that
+    // first iteration completes planes k - R .. k + R (slots 0 .. 2R) and
+    // waits for that.  The compact stencil also reads the boundary cells of
+    // the planes k -+ 1 (edge neighbours), so it waits after every fill.
     if (k == z0) {
-      int sl = cs;
-      for (int q = 0; q < R; ++q, sl = ring_next(sl, NB)) fill(k + q, sl);
-      fill(k + R, sl);
+      for (int q = 0; q <= 2 * R; ++q) fill(z0 - R + q, q);
       __syncthreads();
     } else {
       int sl = cs;
       for (int q = 0; q < R; ++q) sl = ring_next(sl, NB);
       fill(k + R, sl);
+      if (ORDER == kCompact && (xlo || xhi || ylo || yhi)) __syncthreads();  // uniform
     }
     issue(k + R + D, fs_);
     fs_ = ring_next(fs_, NB);
@@ -762,6 +760,45 @@ __global__ void __launch_bounds__(32 * TYT, (tile4_min_blocks<ORDER, TYT, RY, D,
       for (int q = 0; q < 4; ++q) {
         s1[q] = ((xm1v[q] + xp1v[q]) + (ym1v[q] + yp1v[q])) + (zm1v[q] + zp1v[q]);
         s2[q] = R == 2 ? ((xm2v[q] + xp2v[q]) + (ym2v[q] + yp2v[q])) + (zm2v[q] + zp2v[q]) : 0.f;
+      }
+      if (ORDER == kCompact) {
+        // the 12 edge neighbours: x windows (x-1 .. x+4) of rows y-1 and y+1
+        // in plane k and of row y in planes k-1 and k+1, and the centres of
+        // rows y-1 and y+1 in planes k-1 and k+1; boundary cells of planes in
+        // the domain are in the ring, planes outside are zeroed here
+        float bm[6], bp[6], zmw[6], zpw[6];
+        bm[0] = P0[o0 - SX - 1]; bm[5] = P0[o0 - SX + 4];
+        bp[0] = P0[o0 + SX - 1]; bp[5] = P0[o0 + SX + 4];
+        zmw[0] = Pm1[o0 - 1]; zmw[5] = Pm1[o0 + 4];
+        zpw[0] = Pp1[o0 - 1]; zpw[5] = Pp1[o0 + 4];
+        bm[1] = ym1.x; bm[2] = ym1.y; bm[3] = ym1.z; bm[4] = ym1.w;
+        bp[1] = yp1.x; bp[2] = yp1.y; bp[3] = yp1.z; bp[4] = yp1.w;
+        zmw[1] = zm1.x; zmw[2] = zm1.y; zmw[3] = zm1.z; zmw[4] = zm1.w;
+        zpw[1] = zp1.x; zpw[2] = zp1.y; zpw[3] = zp1.z; zpw[4] = zp1.w;
+        const float4 yzmm = *reinterpret_cast<const float4*>(Pm1 + o0 - SX);
+        const float4 yzpm = *reinterpret_cast<const float4*>(Pm1 + o0 + SX);
+        const float4 yzmp = *reinterpret_cast<const float4*>(Pp1 + o0 - SX);
+        const float4 yzpp = *reinterpret_cast<const float4*>(Pp1 + o0 + SX);
+        float eyz_mm[4] = {yzmm.x, yzmm.y, yzmm.z, yzmm.w}, eyz_pm[4] = {yzpm.x, yzpm.y, yzpm.z, yzpm.w};
+        float eyz_mp[4] = {yzmp.x, yzmp.y, yzmp.z, yzmp.w}, eyz_pp[4] = {yzpp.x, yzpp.y, yzpp.z, yzpp.w};
+        if (zedge) {
+          if (k == 0) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) zmw[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) eyz_mm[q] = eyz_pm[q] = 0.f;
+          }
+          if (k == N - 1) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) zpw[q] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) eyz_mp[q] = eyz_pp[q] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          s2[q] = (((bm[q] + bm[q + 2]) + (bp[q] + bp[q + 2])) + ((zmw[q] + zmw[q + 2]) + (zpw[q] + zpw[q + 2]))) +
+                  ((eyz_mm[q] + eyz_pm[q]) + (eyz_mp[q] + eyz_pp[q]));
       }
       if (nx > 0 && j < N) o.apply4(idx0 + r * g.px, nx, c, s1, s2, ex[r]);
     }
