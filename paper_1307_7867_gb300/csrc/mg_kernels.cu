@@ -3,7 +3,7 @@
 // weighting restriction, trilinear prolongation, the FP64 update, max-norms
 // and the dense <-> pitched copies.  One thread per grid point of one item;
 // blockIdx.z = item * N + plane.  (The stencil kernels are in
-// stencil_kernels.cu.)
+// stencil_impl.cuh.)
 #include "kernels.cuh"
 
 namespace h3d {

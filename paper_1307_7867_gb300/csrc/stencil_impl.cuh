@@ -1,6 +1,8 @@
-// stencil_kernels.cu -- the 7-point and 13-point (wide) stencil kernels of the
-// spatial operator (Sec. 1, method of lines) and of the multigrid smoother and
-// residuals (Sec. 1.2), templated on the storage type and stencil order.
+// stencil_impl.cuh -- the 7-point, 13-point (wide) and 19-point (compact)
+// stencil kernels of the spatial operator (Sec. 1, method of lines) and of the
+// multigrid smoother and residuals (Sec. 1.2), templated on the storage type
+// and stencil order, with their launcher templates; stencil_f64.cu and
+// stencil_f32.cu instantiate them.
 //
 // Two drivers share one operator interface:
 //  * k_tile (grids with N >= 32): a block owns a 32 x TY tile of x-y points
@@ -25,6 +27,7 @@
 // outputs from the centre u, the sum s1 of the 6 nearest and s2 of the 6
 // second neighbours, and returns the value whose max |.| is accumulated when
 // the launch asks for a norm.
+#pragma once
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -880,36 +883,6 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
 // launchers
 // ---------------------------------------------------------------------------
 
-cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long long u_stride,
-                       double* out, long long out_stride, const double* alpha,
-                       const double* add_src, double* add_dst, long long add_stride,
-                       const int* active, Shape sh, cudaStream_t st, double* wu_out) {
-  if (order == kCompact) {
-    if (add_src) {
-      OpLap<kCompact, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-      op.wu = wu_out;
-      return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
-    }
-    OpLap<kCompact, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-    op.wu = wu_out;
-    return run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
-  }
-  if (add_src) {
-    if (order == 2) {
-      OpLap<2, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-      return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
-    }
-    OpLap<4, true> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-    return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
-  }
-  if (order == 2) {
-    OpLap<2, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-    return run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
-  }
-  OpLap<4, false> op{u, u_stride, out, out_stride, alpha, add_src, add_dst, add_stride, 0.0};
-  return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
-}
-
 template <typename TR>
 cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, long long u_stride,
                            const double* b, long long b_stride, const Coef<double>* coef,
@@ -973,19 +946,5 @@ cudaError_t launch_resid(int order, const Grid& g, int B, const T* e, const T* r
   OpResid<T, 4> op{e, r, rr, g.fs, coef, T(0), T(0)};
   return run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
 }
-
-#define H3D_INST(T)                                                                            \
-  template cudaError_t launch_resid64<T>(int, const Grid&, int, const double*, long long,      \
-                                         const double*, long long, const Coef<double>*, T*, T*, \
-                                         const Coef<T>*, unsigned long long*, const int*, Shape, \
-                                         cudaStream_t);                                         \
-  template cudaError_t launch_jacobi<T>(int, const Grid&, int, const T*, const T*, T*, double*, \
-                                        long long, const Coef<T>*, const int*, Shape,          \
-                                        cudaStream_t);                                          \
-  template cudaError_t launch_resid<T>(int, const Grid&, int, const T*, const T*, T*,          \
-                                       const Coef<T>*, const int*, Shape, cudaStream_t);
-H3D_INST(double)
-H3D_INST(float)
-#undef H3D_INST
 
 }  // namespace h3d

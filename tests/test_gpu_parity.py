@@ -265,6 +265,22 @@ def test_run_mlsdc_cubic_correction_interpolation(H, oracle, order):
     assert rel(uT, ref) <= 1e-11
 
 
+def test_mlsdc_cubic_two_nodes(H, oracle):
+    """Two-node levels (M = 2): the cubic interpolation runs as the one-pass
+    point-wise kernel (no spare integral fields for the separable passes)."""
+    fine, coarse = (31, 4, 2), (15, 2, 2)
+    cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
+                        mg_tol=1e-11, interp=4)
+    ctx = H.Context(cfg)
+    u0 = inputs.smooth_random_field(31, seed=25, kmax=5)
+    uT = np.empty_like(u0)
+    rc, st = H.pfasst_run(ctx, u0, uT)
+    ref, orc, ost = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11, interp=4), 1 / 64, 2,
+                                     u0, nsweeps_fine=2, max_iters=20, tol=1e-10)
+    assert st["iters"] == ost["iters"] and st["vcycles"] == ost["vcycles"]
+    assert rel(uT, ref) <= 1e-11
+
+
 def test_pfasst_cubic_interpolation_fixed_iterations(H, oracle):
     fine, coarse = (31, 4, 5), (15, 2, 3)
     P, K = 4, 3
