@@ -180,15 +180,24 @@ def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None, interp
                          mg_tol=w["mg_tol"], max_cycles=50, precision=prec,
                          forcing=H.FORCING_PAPER_LITERAL, batch=slices or w["slices"],
                          use_graphs=1 if graphs else 0, autotune=1, inner=inner, mg_rel=mg_rel,
-                         interp=w.get("interp", 2) if interp is None else interp)
+                         interp=w.get("interp", 2) if interp is None else interp,
+                         persistent=w.get("persistent", -1))
 
 
 def workload_config(w, world):
     """The JSON line's config: the workload and the options it runs with."""
-    return {"workload": w["desc"], "N_fine": w["fine"][0], "dt": w["dt"],
+    nf = w["fine"][0]
+    field_mb = nf ** 3 * 8 / 1e6
+    if field_mb > 100:
+        l2 = f"working set >> L2 (fields of {field_mb:.0f} MB), no flush needed"
+    else:
+        l2 = (f"working set ({field_mb:.2f} MB per field) fits in L2 and every solve re-reads it "
+              "in each of its V-cycles, so L2 residency is part of the workload; no flush")
+    return {"workload": w["desc"], "N_fine": nf, "dt": w["dt"],
             "mg_rel": w.get("mg_rel", 0.0), "interp": w.get("interp", 2),
+            "persistent_solves": {-1: "N <= 31", 0: "off", 1: "N <= 63"}[w.get("persistent", -1)],
             "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "working set >> L2 (fields of 133 MB+), no flush needed"}
+            "l2": l2}
 
 
 def max_over_ranks(seconds, device, world):
@@ -635,6 +644,9 @@ def main():
     ap.add_argument("--mg-rel", type=float, default=None,
                     help="headline run: solver tolerance max(mg_tol, MG_REL x sweep residual)")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
+    ap.add_argument("--persistent", type=int, default=None, choices=[-1, 0, 1],
+                    help="multigrid solves as one persistent kernel: -1 on grids N <= 31 "
+                         "(default), 0 never, 1 on grids N <= 63")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
     ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
                     help="profiling case: one step of the workload capped at one iteration")
@@ -655,6 +667,8 @@ def main():
                  desc=w["desc"] + f"; solves stop at max(mg_tol, {args.mg_rel} x sweep residual)")
     if args.interp == 4:
         w = dict(w, interp=4, desc=w["desc"] + "; cubic interpolation of the coarse correction")
+    if args.persistent is not None:
+        w = dict(w, persistent=args.persistent)
     if args.sweeps_fine:
         w = dict(w, sweeps_fine=args.sweeps_fine,
                  desc=w["desc"] + f"; {args.sweeps_fine} fine sweeps per iteration")

@@ -120,6 +120,13 @@ typedef struct {
                                step (Sec. 1.1; the paper does not say which): 2 trilinear
                                (default), 4 tensor-product cubic (4-point midpoint rule,
                                odd reflection at the boundary) */
+  int persistent;           /* multigrid solves as one persistent cooperative kernel each
+                               (residual, all V-cycles and the stop rule in one launch, grid
+                               barriers between the steps; bitwise the results of the launch
+                               sequence): -1 (default) on levels with 15 <= N <= 31, 1 on
+                               levels with 15 <= N <= 63, 0 never.  Orders 2 and 4 only (the
+                               compact stencil's levels use the launch sequence).  A grid
+                               barrier that waits about 1 s gives up: HEAT3D_ETIMEOUT */
 } heat3d_config;
 
 typedef struct {
@@ -229,6 +236,15 @@ int heat3d_profile(heat3d_ctx* ctx, int kernel_class);
  * Synchronises the stream. */
 int heat3d_profile_read(heat3d_ctx* ctx, double* ms, long long* launches, double* bytes,
                         double* dp_ops, double* flops);
+
+/* Self-test of the bounded grid barrier that the persistent solve kernel
+ * (heat3d_config.persistent) waits on between its steps: a cooperative launch
+ * of 4 blocks on `stream` (a cudaStream_t; NULL: legacy) meets at one barrier.
+ * absent_block = -1: all arrive, HEAT3D_OK.  absent_block in 0..3: that block
+ * returns without arriving, the others give up after about 1 s of waiting and
+ * return, and the call reports HEAT3D_ETIMEOUT (the device stays usable).
+ * Synchronises the stream; other values: HEAT3D_EINVAL. */
+int heat3d_selftest_barrier(void* stream, int absent_block);
 
 /* ---------------------------------------------------------------------- */
 /* Solve without any device allocation (no counterpart in the paper).       */

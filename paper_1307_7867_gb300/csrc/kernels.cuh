@@ -99,6 +99,44 @@ cudaError_t launch_vcycle_small(int order, int nlev, const int* Ns, const Coef<T
                                 int B, const T* b, T* e, const Grid& gtop, int nu1, int nu2,
                                 const int* active, cudaStream_t st);
 
+// The whole solve of mg_vcycle's rule for B items on a grid with 15 <= N <=
+// kPersistMaxN (orders 2 and 4) as one persistent cooperative kernel
+// (persist.cu): FP64 residual and norm, `inner` V(nu1, nu2) cycles per
+// residual, the stop rule of launch_mg_check after each residual, until every
+// item has stopped or max_cycles cycles ran; bitwise the results of the
+// launch sequence.  Pointers address item 0 of the launch; the multigrid
+// fields of level k are at stride g[k].fs, u and rhs (FP64, grid g[0]) at
+// strides us and bs.  active: B flags, 1 on entry; ncyc and nan_flag zeroed by
+// the caller; tol, last as launch_mg_check; norm2: 2 B scratch words and ctl:
+// 4 words of barrier state, both zeroed here.  ctl[1] is set when a grid
+// barrier gave up waiting (about 1 s), and the kernel then returned early.
+constexpr int kPersistMaxN = 63;
+template <typename T>
+struct MgPersist {
+  int nlev;  // multigrid levels, g[nlev - 1].N == 1
+  Grid g[kMaxLevels];
+  T* b[kMaxLevels];
+  T* e[kMaxLevels];
+  T* t[kMaxLevels];
+  const Coef<T>* cf[kMaxLevels];
+  const Coef<double>* c64;
+  double* u;
+  long long us;
+  const double* rhs;
+  long long bs;
+  int B, nu1, nu2, inner, max_cycles;
+  unsigned long long* norm2;
+  int* active;
+  int* ncyc;
+  double* last;
+  const double* tol;
+  int* nan_flag;
+  int* ctl;
+};
+bool mg_persist_supported(int order, int N);
+template <typename T>
+cudaError_t launch_mg_persist(int order, const MgPersist<T>& p, cudaStream_t st);
+
 // u64 += e
 template <typename T>
 cudaError_t launch_update(const Grid& g, int B, const T* e, double* u64, long long u64_stride,

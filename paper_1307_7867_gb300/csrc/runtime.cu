@@ -196,6 +196,8 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
     return h3d_fail(c, HEAT3D_EINVAL, "mg.rel must lie in [0, 1)");
   if (cfg->interp != 0 && cfg->interp != 2 && cfg->interp != 4)
     return h3d_fail(c, HEAT3D_EINVAL, "interp must be 2 (trilinear) or 4 (cubic)");
+  if (cfg->persistent < -1 || cfg->persistent > 1)
+    return h3d_fail(c, HEAT3D_EINVAL, "persistent must be -1 (automatic), 0 or 1");
   if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED)
     return h3d_fail(c, HEAT3D_EINVAL, "precision must be HEAT3D_FP64 or HEAT3D_MIXED");
   if (cfg->slices < 1 || cfg->sweeps_fine < 0 || cfg->sweeps_coarse < 0 || cfg->iters < 0)
@@ -300,6 +302,8 @@ static size_t plan(heat3d_ctx* c, char* base) {
     L.mg_ncyc = (int*)take(sizeof(int) * B);
     L.mg_last = (double*)take(sizeof(double) * B);
     L.mg_flag = (int*)take(sizeof(int) * 2);  // NaN flag, cycle cap
+    L.pnorm = (unsigned long long*)take(sizeof(unsigned long long) * 2 * B);
+    L.pctl = (int*)take(sizeof(int) * 4);
   }
   c->map_d = (FasMap*)take(sizeof(FasMap));
   off = (off + 255) / 256 * 256;
@@ -666,6 +670,62 @@ static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const 
   return HEAT3D_OK;
 }
 
+// Stats and return code of a solve whose stop rule ran on the device: per
+// item the cycles done, the last residual norm and its tolerance.
+static int solve_outcome(heat3d_ctx* c, int lev, int B, int inner, bool fixed, double tol,
+                         int max_cycles, const std::vector<double>& tl,
+                         const std::vector<int>& hcyc, const std::vector<double>& last, int nan,
+                         heat3d_stats* s) {
+  if (nan) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
+  long long total = 0;
+  double mx = 0;
+  int notconv = 0;
+  for (int b = 0; b < B; ++b) {
+    total += hcyc[b];
+    mx = std::max(mx, last[b]);
+    if (!fixed && !(last[b] <= tl[b])) ++notconv;
+  }
+  if (s) {
+    s->vcycles += total * inner;
+    s->vcycles_level[lev] += total * inner;
+    s->solves += B;
+    s->mg_residual = mx;
+  }
+  if (notconv > 0) {
+    if (s) s->notconv += notconv;
+    return h3d_fail(c, HEAT3D_ENOTCONV, "multigrid: %d item(s) above tol %.3g after %d cycles",
+                    notconv, tol, max_cycles);
+  }
+  return HEAT3D_OK;
+}
+
+// Algorithmic bytes of one item's refinement step (inner V-cycles and the
+// FP64 residual) in the persistent kernel: the launch sequence's operations,
+// with the levels from N <= 7 down in shared memory.
+template <typename T>
+static double persist_step_bytes(const SdcLevel& L, int inner, int nu1, int nu2) {
+  const double ts = sizeof(T);
+  int kb = 1;
+  while (kb < L.nmg && L.mg[kb].N > 7) ++kb;
+  double by = 0.0;
+  for (int q = 0; q < inner; ++q) {
+    const bool warm = q > 0, final = q == inner - 1;
+    for (int k = 0; k < kb; ++k) {
+      const double n = (double)L.mg[k].N * L.mg[k].N * L.mg[k].N;
+      if (k > 0) by += 2.0 * ts * n;
+      by += (k == 0 && warm ? nu1 : nu1 - 1) * 3.0 * ts * n;
+      by += 3.0 * ts * n + ts * n * (1.0 + 1.0 / 8.0);
+      by += ts * n * (2.0 + 1.0 / 8.0);
+      for (int s = 0; s < nu2; ++s) by += (k == 0 && final && s == nu2 - 1) ? (2.0 * ts + 16.0) * n : 3.0 * ts * n;
+      if (k == 0 && final && nu2 == 0) by += (ts + 16.0) * n;
+    }
+    const double nb = (double)L.mg[kb].N * L.mg[kb].N * L.mg[kb].N;
+    by += 2.0 * ts * nb;
+  }
+  const double n0 = (double)L.mg[0].N * L.mg[0].N * L.mg[0].N;
+  return by + (16.0 + 2.0 * ts) * n0;
+}
+
 template <typename T>
 static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u, long long us,
                       const double* rhs, long long bs, int max_cycles, double tol,
@@ -698,6 +758,56 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     return HEAT3D_OK;
   };
   const int inner = std::max(1, c->cfg.mg.inner);
+  if (L.persist) {
+    // the whole solve in one persistent kernel (same cycles and results)
+    std::vector<double> tl(B);
+    for (int b = 0; b < B; ++b) tl[b] = fixed ? -1.0 : (tolv ? tolv[b] : tol);
+    CK(cudaMemcpyAsync(L.mg_tol_d + b0, tl.data(), sizeof(double) * B, cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(L.mg_ncyc + b0, 0, sizeof(int) * B, st));
+    CK(cudaMemsetAsync(L.mg_flag, 0, sizeof(int), st));
+    MgPersist<T> p{};
+    p.nlev = L.nmg;
+    for (int k = 0; k < L.nmg; ++k) {
+      p.g[k] = L.mg[k];
+      p.b[k] = mgbuf<T>(L, k, 0, b0);
+      p.e[k] = mgbuf<T>(L, k, 1, b0);
+      p.t[k] = mgbuf<T>(L, k, 2, b0);
+      p.cf[k] = coefT<T>(L, slot, k, b0);
+    }
+    p.c64 = c64;
+    p.u = u;
+    p.us = us;
+    p.rhs = rhs;
+    p.bs = bs;
+    p.B = B;
+    p.nu1 = c->cfg.mg.nu1;
+    p.nu2 = c->cfg.mg.nu2;
+    p.inner = inner;
+    p.max_cycles = max_cycles;
+    p.norm2 = L.pnorm;
+    p.active = act;
+    p.ncyc = L.mg_ncyc + b0;
+    p.last = L.mg_last + b0;
+    p.tol = L.mg_tol_d + b0;
+    p.nan_flag = L.mg_flag;
+    p.ctl = L.pctl;
+    CK(launch_mg_persist<T>(order, p, st));
+    std::vector<int> hcyc(B);
+    std::vector<double> last(B);
+    int hnan = 0, hctl[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(hcyc.data(), L.mg_ncyc + b0, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(last.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hnan, L.mg_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(hctl, L.pctl, sizeof(hctl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hctl[1])  // the barrier's error word
+      return h3d_fail(c, HEAT3D_ETIMEOUT, "persistent multigrid solve: a grid barrier gave up waiting");
+    long long done = 0;
+    for (int b = 0; b < B; ++b) done += hcyc[b];
+    c->bytes += (double)done * persist_step_bytes<T>(L, inner, c->cfg.mg.nu1, c->cfg.mg.nu2) +
+                (16.0 + 2.0 * sizeof(T)) * pts;
+    return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hnan, s);
+  }
   auto one_cycle = [&]() -> int {
     T* cur = nullptr;
     for (int q = 0; q < inner; ++q)
@@ -760,27 +870,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     CK(cudaMemcpyAsync(last.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hflag, L.mg_flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    if (hflag[0]) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
-    long long total = 0;
-    double mx = 0;
-    int notconv = 0;
-    for (int b = 0; b < B; ++b) {
-      total += hcyc[b];
-      mx = std::max(mx, last[b]);
-      if (!fixed && !(last[b] <= tl[b])) ++notconv;
-    }
-    if (s) {
-      s->vcycles += total * inner;
-      s->vcycles_level[lev] += total * inner;
-      s->solves += B;
-      s->mg_residual = mx;
-    }
-    if (notconv > 0) {
-      if (s) s->notconv += notconv;
-      return h3d_fail(c, HEAT3D_ENOTCONV, "multigrid: %d item(s) above tol %.3g after %d cycles",
-                      notconv, tol, max_cycles);
-    }
-    return HEAT3D_OK;
+    return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hflag[0], s);
   }
   RET(residual());
   int cycles = 0, live = B;
@@ -1398,6 +1488,7 @@ void heat3d_config_default(heat3d_config* cfg) {
   cfg->autotune = 1;
   cfg->fuse_coarse = 1;
   cfg->interp = 2;
+  cfg->persistent = -1;
 }
 
 int heat3d_workspace_size(const heat3d_config* cfg, size_t* bytes) {
@@ -1450,6 +1541,16 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   }
   CK(cudaStreamSynchronize(c->st));
   c->bound = true;
+  // persistent solve kernel: grids with N <= 31 by default, up to
+  // kPersistMaxN when forced (orders 2 and 4, cooperative launch needed)
+  int coop = 0;
+  CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->cfg.device));
+  for (int l = 0; l < c->cfg.nlevels; ++l) {
+    SdcLevel& L = c->lv[l];
+    const int lim = c->cfg.persistent > 0 ? kPersistMaxN : 31;
+    L.persist = c->cfg.persistent != 0 && coop && mg_persist_supported(L.L.order, L.L.N) &&
+                L.L.N <= lim;
+  }
   if (c->cfg.autotune) RET(h3d_autotune(c));
   // HEAT3D_FUSE_MAX=n forces the coarse-level fusion depth (testing)
   if (const char* f = getenv("HEAT3D_FUSE_MAX")) {

@@ -61,6 +61,11 @@ struct SdcLevel {
   // multigrid levels with N <= fuse_max run as one fused kernel per V-cycle
   // (when fuse_coarse is on); chosen by the autotuner among 15, 7, 3 and 0
   int fuse_max = 15;
+  // every solve of this level runs as one persistent kernel (small grids):
+  // its norm slots and barrier state
+  bool persist = false;
+  unsigned long long* pnorm = nullptr;
+  int* pctl = nullptr;
 };
 
 // A captured chunk of solve cycles (each: V-cycle(s), norm reset, refinement

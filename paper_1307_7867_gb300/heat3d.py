@@ -31,7 +31,7 @@ ABI_FUNCTIONS = [
     "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
     "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
     "heat3d_set_interval", "heat3d_kernel_launches", "heat3d_profile", "heat3d_profile_read",
-    "mg_vcycle_noalloc", "mg_vcycle_noalloc_last_error",
+    "heat3d_selftest_barrier", "mg_vcycle_noalloc", "mg_vcycle_noalloc_last_error",
     "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
     "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
 ]
@@ -59,7 +59,7 @@ class Config(C.Structure):
                 ("predictor", C.c_int), ("mg", MG), ("precision", C.c_int), ("forcing", C.c_int),
                 ("batch", C.c_int), ("device", C.c_int), ("stream", C.c_void_p),
                 ("use_graphs", C.c_int), ("autotune", C.c_int), ("fuse_coarse", C.c_int),
-                ("interp", C.c_int)]
+                ("interp", C.c_int), ("persistent", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -126,6 +126,7 @@ def load():
     L.heat3d_kernel_launches.restype = C.c_longlong
     L.heat3d_profile.argtypes = [V, I]
     L.heat3d_profile_read.argtypes = [V, P(D), P(C.c_longlong), P(D), P(D), P(D)]
+    L.heat3d_selftest_barrier.argtypes = [V, I]
     L.mg_vcycle_noalloc.argtypes = [I, I, I, D, V, V, I, D, V, P(Stats)]
     L.mg_vcycle_noalloc_last_error.argtypes = []
     L.mg_vcycle_noalloc_last_error.restype = C.c_char_p
@@ -262,7 +263,8 @@ def pfasst_run(ctx: Context, u0, uT, allow_notconv=False):
 def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2, sweeps_coarse=1,
                 slices=1, iters=20, tol_sdc=1e-10, predictor=1, nu1=2, nu2=1, max_cycles=50,
                 mg_tol=1e-10, precision=FP64, forcing=FORCING_PAPER_LITERAL, batch=1, device=0,
-                use_graphs=0, autotune=1, inner=1, fuse_coarse=1, mg_rel=0.0, interp=2) -> Config:
+                use_graphs=0, autotune=1, inner=1, fuse_coarse=1, mg_rel=0.0, interp=2,
+                persistent=-1) -> Config:
     """fine, coarse: (N, order, M) tuples; coarse None gives single-level SDC."""
     cfg = heat3d_config_default()
     cfg.nu, cfg.T, cfg.dt = nu, T, dt
@@ -278,6 +280,7 @@ def make_config(fine, coarse=None, *, nu=0.1, T=1.0, dt=1.0 / 64, sweeps_fine=2,
     cfg.autotune = autotune
     cfg.fuse_coarse = fuse_coarse
     cfg.interp = interp
+    cfg.persistent = persistent
     return cfg
 
 
@@ -300,6 +303,13 @@ def heat3d_profile_read(ctx: Context) -> dict:
                                       C.byref(fl)), ctx.h)
     return {"ms": ms.value, "launches": n.value, "bytes": b.value, "dp_ops": dp.value,
             "flops": fl.value}
+
+
+def heat3d_selftest_barrier(absent_block, stream=None) -> int:
+    """Return code of the bounded grid-barrier self-test (OK, or ETIMEOUT when
+    block `absent_block` of the four stays away)."""
+    sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    return load().heat3d_selftest_barrier(sp, int(absent_block))
 
 
 def mg_vcycle_noalloc(N, order, precision, c, rhs, u, max_cycles, tol, stream=None,

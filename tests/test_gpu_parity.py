@@ -324,15 +324,16 @@ def test_run_mixed_precision_matches_fp64_oracle(H, oracle):
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graphs_and_autotune_change_nothing(H, oracle, precision):
     """V-cycles replayed from CUDA graphs (private stream), autotuned launch
-    shapes and the fused coarse-level kernel give bitwise the same MLSDC
-    result as plain launches with the default shapes; the FP64 run also
-    matches the oracle."""
+    shapes, the fused coarse-level kernel and the persistent solve kernel give
+    bitwise the same MLSDC result as plain launches with the default shapes;
+    the FP64 run also matches the oracle."""
     fine, coarse = (31, 4, 5), (15, 2, 3)
     prec = H.FP64 if precision == "fp64" else H.MIXED
     outs = []
-    for graphs, tune, fuse in ((0, 0, 0), (1, 1, 1), (1, 0, 0), (0, 1, 1)):
+    for graphs, tune, fuse, pers in ((0, 0, 0, 0), (1, 1, 1, 0), (1, 0, 0, 0), (0, 1, 1, 0),
+                                     (1, 1, 1, -1)):
         cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, precision=prec, mg_tol=1e-11,
-                            use_graphs=graphs, autotune=tune, fuse_coarse=fuse)
+                            use_graphs=graphs, autotune=tune, fuse_coarse=fuse, persistent=pers)
         ctx = H.Context(cfg, stream=torch.cuda.Stream())
         u0 = inputs.sine_mode(31)
         uT = np.empty_like(u0)
@@ -388,7 +389,8 @@ def test_every_fusion_depth_is_bitwise_identical(H, precision, monkeypatch):
     for fm in (15, 7, 3, 0):
         monkeypatch.setenv("HEAT3D_FUSE_MAX", str(fm))
         cfg = H.make_config((63, 4, 5), (31, 2, 3), dt=1 / 32, T=2 / 32, precision=prec,
-                            mg_tol=1e-11, use_graphs=1, inner=2 if prec == H.MIXED else 1)
+                            mg_tol=1e-11, use_graphs=1, inner=2 if prec == H.MIXED else 1,
+                            persistent=0)
         ctx = H.Context(cfg, stream=torch.cuda.Stream())
         u0 = inputs.smooth_random_field(63, seed=23, kmax=5)
         uT = np.empty_like(u0)
@@ -430,7 +432,8 @@ def test_chunked_device_stop_rule_matches_host_loop(H, oracle):
     b = inputs.random_field(N, seed=21)
     outs = {}
     for graphs in (0, 1):
-        ctx = H.Context(H.make_config((N, 4, 3), use_graphs=graphs), stream=torch.cuda.Stream())
+        ctx = H.Context(H.make_config((N, 4, 3), use_graphs=graphs, persistent=0),
+                        stream=torch.cuda.Stream())
         u = dev(np.zeros_like(b))
         rc, st = H.mg_vcycle(ctx, 0, c, dev(b), u, 50, 1e-12)
         uf = dev(np.zeros_like(b))
@@ -447,7 +450,7 @@ def test_chunked_device_stop_rule_matches_host_loop(H, oracle):
     res = []
     for graphs in (0, 1):
         cfg = H.make_config((31, 4, 5), (15, 2, 3), dt=1 / 16, T=4 / 16, sweeps_fine=1, slices=4,
-                            iters=3, tol_sdc=-1.0, mg_tol=1e-11, use_graphs=graphs)
+                            iters=3, tol_sdc=-1.0, mg_tol=1e-11, use_graphs=graphs, persistent=0)
         ctx = H.Context(cfg, stream=torch.cuda.Stream())
         u0 = inputs.smooth_random_field(31, seed=22, kmax=4)
         uT = np.empty_like(u0)
