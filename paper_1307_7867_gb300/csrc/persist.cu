@@ -22,10 +22,11 @@
 //
 // Data that another block wrote during the launch is read through L2
 // (ld.global.cg), never through the non-coherent read-only path.  The grid
-// barrier is a counter and a generation word; a waiting block gives up after
-// about one second, sets an error word that every other waiting block sees,
-// and all blocks return; the host then reports HEAT3D_ETIMEOUT.  The
-// cooperative launch guarantees that all blocks are resident at once.
+// barrier is one arrival counter; a waiting block gives up after about one
+// second, sets an error word that every other waiting block sees, and all
+// blocks return; the host then reports HEAT3D_ETIMEOUT.  The cooperative
+// launch guarantees that all blocks are resident at once.
+
 #include <algorithm>
 
 #include "../../include/heat3d.h"
@@ -39,13 +40,10 @@ constexpr int kPersistThreads = 256;
 constexpr unsigned long long kBarrierNs = 1000000000ull;  // give up after 1 s
 constexpr unsigned kBarrierSpins = 1u << 23;              // second bound on the spin
 
-// gen and err share one 8-byte word, so that a waiting block reads both
-// with a single load per poll.
 struct alignas(16) PersistCtl {
-  unsigned gen;    // barriers completed
+  unsigned count;  // arrivals so far in this launch (never reset within it)
   unsigned err;    // 1: a barrier timed out
-  unsigned count;  // blocks arrived at the current barrier
-  unsigned pad;
+  unsigned pad[2];
 };
 
 template <typename T>
@@ -55,9 +53,9 @@ struct PersistArgs {
   SmallArgs<T> small;  // levels kb .. nlev-1 for vcycle_small_body
 };
 
-__device__ __forceinline__ unsigned long long ld_acquire64(const void* p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -68,37 +66,32 @@ __device__ __forceinline__ unsigned long long now_ns() {
 }
 
 // Grid-wide barrier with a bounded wait; false when it timed out here or in
-// another block (every block then leaves the kernel).
+// another block (every block then leaves the kernel).  Barrier g of the
+// launch completes when the arrival counter reaches g * gridDim.x: each block
+// adds one (after a fence that publishes the block's writes) and polls the
+// counter with acquire loads, so no reset or separate release write sits on
+// the critical path.
 __device__ bool grid_barrier(PersistCtl* ctl, unsigned& gen) {
   __shared__ int ok_s;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned want = gen + 1;
+    const unsigned target = (gen + 1) * gridDim.x;
     __threadfence();
-    if (atomicAdd(&ctl->count, 1u) == gridDim.x - 1) {
-      atomicExch(&ctl->count, 0u);
-      __threadfence();
-      atomicExch(&ctl->gen, want);
-    } else {
-      const unsigned long long t0 = now_ns();
-      for (unsigned it = 1;; ++it) {
-        const unsigned long long w = ld_acquire64(&ctl->gen);  // gen (low), err (high)
-        if ((unsigned)w == want) break;
-        if (w >> 32) {
-          ok = 0;
-          break;
-        }
-        if ((it & 15) == 0 && (it >= kBarrierSpins || now_ns() - t0 > kBarrierNs)) {
+    atomicAdd(&ctl->count, 1u);
+    unsigned long long t0 = 0ull;
+    for (unsigned it = 1; ld_acquire(&ctl->count) < target; ++it) {
+      if ((it & 15) == 0) {
+        if (t0 == 0ull) t0 = now_ns();
+        if (*(volatile unsigned*)&ctl->err || it >= kBarrierSpins || now_ns() - t0 > kBarrierNs) {
           atomicExch(&ctl->err, 1u);
           ok = 0;
           break;
         }
-        __nanosleep(32);
       }
+      __nanosleep(32);
     }
-    __threadfence();
-    gen = want;
+    ++gen;
     ok_s = ok;
   }
   __syncthreads();
