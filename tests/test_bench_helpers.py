@@ -37,3 +37,14 @@ def test_workload_config_keys():
     assert cfg["N_fine"] == 255 and cfg["interp"] == 2 and cfg["mg_rel"] == 0.0
     assert cfg["parallelism"] == "single GPU"
     assert bench.workload_config(bench.WORKLOADS["c2"], 4)["parallelism"] == "replicas x4"
+
+
+def test_workload_config_names_the_solve_path_and_l2_regime():
+    """The persistent solve kernel's setting and whether the working set fits
+    in L2 are stated in the JSON line's config."""
+    c1 = bench.workload_config(bench.WORKLOADS["c1"], 1)
+    c2 = bench.workload_config(bench.WORKLOADS["c2"], 1)
+    assert c1["persistent_solves"] == "N <= 31" and c2["persistent_solves"] == "N <= 31"
+    assert "fits in L2" in c1["l2"] and "no flush needed" in c2["l2"]
+    off = bench.workload_config(dict(bench.WORKLOADS["c1"], persistent=0), 1)
+    assert off["persistent_solves"] == "off"
