@@ -30,7 +30,11 @@
  *   - SDC initial iterate: the initial value spread to every node;
  *   - FAS: injection in space and time, trilinear (or, with interp = 4,
  *     tensor-product cubic) + Lagrange interpolation of the coarse
- *     correction; PFASST schedule and predictor as coded below;
+ *     correction; PFASST schedule and predictor as coded below (pinned by
+ *     its converged limit, the serial collocation solution, and by the
+ *     one-slice case equal to MLSDC; the iterates of a fixed iteration count
+ *     in between follow this schedule reading and are "parity unpinned": no
+ *     published iterate exists to compare them with);
  *   - optional solver tolerance tied to the sweep's incoming residual
  *     (mg_rel), and the W-solve of the compact FAS restriction applied to the
  *     weighted residual (U_j - U_0 + W^{-1} r), see or_fas_restrict_st.
