@@ -28,9 +28,9 @@
  *     unknown solved exactly (Sec. 1.2);
  *   - solve stop rule: max|b - A u| <= tol, checked before every cycle;
  *   - SDC initial iterate: the initial value spread to every node;
- *   - FAS: injection in space and time, trilinear (or, with interp = 4,
- *     tensor-product cubic) + Lagrange interpolation of the coarse
- *     correction; PFASST schedule and predictor as coded below (pinned by
+ *   - FAS: injection in space and time, trilinear (or, with interp = 4, 6,
+ *     8, the tensor-product 4-, 6- or 8-point midpoint rule) + Lagrange
+ *     interpolation in time of the coarse correction; PFASST schedule and predictor as coded below (pinned by
  *     its converged limit, the serial collocation solution, and by the
  *     one-slice case equal to MLSDC; the iterates of a fixed iteration count
  *     in between follow this schedule reading and are "parity unpinned": no
@@ -68,8 +68,9 @@ typedef struct {
   int nu1, nu2;   /* pre- and post-smoothing sweeps, V(nu1, nu2) */
   double mg_rel;  /* > 0: a sweep's solves stop at max(mg_tol, mg_rel * residual of the
                      sweep's incoming iterate) */
-  int interp;     /* spatial interpolation of the FAS correction: 4 = cubic
-                     (4-point, odd reflection at the boundary), else trilinear */
+  int interp;     /* spatial interpolation of the FAS correction: 4, 6, 8 = the
+                     tensor-product 4-, 6- or 8-point midpoint rule (odd extension
+                     about the boundary), else trilinear */
 } or_problem;
 
 typedef struct {
@@ -291,24 +292,75 @@ static double cubic_line_at(const double* e, int stride, int Nc, int i) {
   return (-v[0] + 9.0 * v[1] + 9.0 * v[2] - v[3]) / 16.0;
 }
 
-/* uf += P3 e: tensor-product cubic interpolation, x, then y, then z. */
-void or_prolong_add_cubic(int Nc, const double* e, double* uf) {
+/* Weight of point q (0..npts-1) of the npts-point Lagrange rule on equally
+ * spaced points, evaluated halfway between the middle two: with the points at
+ * X_q / 2, X_q = 2q - (npts - 1) (odd integers), the weight is the product
+ * over r != q of (0 - X_r) / (X_q - X_r), formed in integers and divided once
+ * (npts = 4 gives (-1, 9, 9, -1) / 16). */
+static double lagrange_mid_weight(int npts, int q) {
+  long long num = 1, den = 1;
+  for (int r = 0; r < npts; ++r) {
+    if (r == q) continue;
+    long long xr = 2 * r - (npts - 1), xq = 2 * q - (npts - 1);
+    num *= -xr;
+    den *= xq - xr;
+  }
+  return (double)num / (double)den;
+}
+
+/* Coarse line value at coarse index a (any integer) of the odd extension
+ * about both boundary points (0 and Nc + 1, where the value is zero): period
+ * 2 (Nc + 1), odd about 0. */
+static double odd_ext_at(const double* e, int stride, int Nc, int a) {
+  int per = 2 * (Nc + 1);
+  int r = ((a % per) + per) % per;
+  if (r == 0 || r == Nc + 1) return 0.0;
+  if (r > Nc + 1) return -e[(size_t)(per - r - 1) * stride];
+  return e[(size_t)(r - 1) * stride];
+}
+
+/* One axis of the npts-point (npts = 6 or 8) midpoint rule: even fine
+ * indices take the coarse value, odd ones sum the weighted npts coarse values
+ * centred on the midpoint, in order of the points, on the odd extension. */
+static double lagrange_line_at(const double* e, int stride, int Nc, int i, int npts) {
+  if (i % 2 == 0) return e[(size_t)(i / 2 - 1) * stride];
+  int I = (i - 1) / 2; /* the midpoint lies between coarse I and I + 1 */
+  double s = 0.0;
+  for (int q = 0; q < npts; ++q)
+    s += lagrange_mid_weight(npts, q) * odd_ext_at(e, stride, Nc, I - npts / 2 + 1 + q);
+  return s;
+}
+
+static double line_at(const double* e, int stride, int Nc, int i, int npts) {
+  return npts == 4 ? cubic_line_at(e, stride, Nc, i) : lagrange_line_at(e, stride, Nc, i, npts);
+}
+
+/* uf += P e: tensor-product npts-point midpoint interpolation (npts = 4:
+ * cubic, 6, 8), x, then y, then z. */
+void or_prolong_add_lagrange(int Nc, int npts, const double* e, double* uf) {
   int Nf = 2 * Nc + 1;
   double* tx = (double*)malloc((size_t)Nf * Nc * Nc * sizeof(double));
   double* txy = (double*)malloc((size_t)Nf * Nf * Nc * sizeof(double));
   for (int K = 0; K < Nc; ++K)
     for (int J = 0; J < Nc; ++J)
       for (int i = 1; i <= Nf; ++i)
-        tx[((size_t)K * Nc + J) * Nf + (i - 1)] = cubic_line_at(e + ((size_t)K * Nc + J) * Nc, 1, Nc, i);
+        tx[((size_t)K * Nc + J) * Nf + (i - 1)] =
+            line_at(e + ((size_t)K * Nc + J) * Nc, 1, Nc, i, npts);
   for (int K = 0; K < Nc; ++K)
     for (int j = 1; j <= Nf; ++j)
       for (int i = 0; i < Nf; ++i)
-        txy[((size_t)K * Nf + (j - 1)) * Nf + i] = cubic_line_at(tx + (size_t)K * Nc * Nf + i, Nf, Nc, j);
+        txy[((size_t)K * Nf + (j - 1)) * Nf + i] =
+            line_at(tx + (size_t)K * Nc * Nf + i, Nf, Nc, j, npts);
   for (int k = 1; k <= Nf; ++k)
     for (int j = 0; j < Nf; ++j)
       for (int i = 0; i < Nf; ++i)
-        uf[((size_t)(k - 1) * Nf + j) * Nf + i] += cubic_line_at(txy + (size_t)j * Nf + i, Nf * Nf, Nc, k);
+        uf[((size_t)(k - 1) * Nf + j) * Nf + i] += line_at(txy + (size_t)j * Nf + i, Nf * Nf, Nc, k, npts);
   free(tx); free(txy);
+}
+
+/* uf += P3 e: tensor-product cubic interpolation, x, then y, then z. */
+void or_prolong_add_cubic(int Nc, const double* e, double* uf) {
+  or_prolong_add_lagrange(Nc, 4, e, uf);
 }
 
 /* Exact solve on the one-unknown grid: A11 is read off by applying A to the
@@ -724,8 +776,9 @@ int or_fas_restrict(const or_level* LF, const or_level* LG, const or_problem* P,
 }
 
 /* Coarse-to-fine correction: Delta_m = U^G_m - UGr_m at the coarse nodes,
- * Lagrange interpolation in time to every fine node, trilinear interpolation
- * in space, U^F_j += that, then F^F is recomputed from the new U^F. */
+ * Lagrange interpolation in time to every fine node, trilinear (or the
+ * interp-point midpoint rule) in space, U^F_j += that, then F^F is recomputed
+ * from the new U^F. */
 int or_fas_interpolate(const or_level* LF, const or_level* LG, const or_problem* P,
                        const double* UG, const double* UGr, double* UF, double* FF) {
   if (fas_check(LF, LG) != OR_OK) return OR_EINVAL;
@@ -743,8 +796,8 @@ int or_fas_interpolate(const or_level* LF, const or_level* LG, const or_problem*
     }
     if (NF == NG) {
       for (size_t p = 0; p < nf; ++p) UF[(size_t)j * nf + p] += d[p];
-    } else if (P->interp == 4) {
-      or_prolong_add_cubic(NG, d, UF + (size_t)j * nf);
+    } else if (P->interp == 4 || P->interp == 6 || P->interp == 8) {
+      or_prolong_add_lagrange(NG, P->interp, d, UF + (size_t)j * nf);
     } else {
       or_prolong_add(NG, d, UF + (size_t)j * nf);
     }

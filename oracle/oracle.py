@@ -74,6 +74,7 @@ def lib():
         L.or_restrict_fw.argtypes = [I, _dp, _dp]
         L.or_prolong_add.argtypes = [I, _dp, _dp]
         L.or_prolong_add_cubic.argtypes = [I, _dp, _dp]
+        L.or_prolong_add_lagrange.argtypes = [I, I, _dp, _dp]
         L.or_vcycle.argtypes = [I, I, D, _dp, _dp, I, I]
         L.or_mg_solve.argtypes = [I, I, D, _dp, _dp, D, I, I, I, P(I), P(D)]
         L.or_mg_solve.restype = I
@@ -174,6 +175,15 @@ def prolong_add_cubic(e, uf):
     e = _c(e)
     uf = _c(uf).copy()
     lib().or_prolong_add_cubic(e.shape[0], e, uf)
+    return uf
+
+
+def prolong_add_lagrange(e, uf, npts):
+    """uf += tensor-product npts-point midpoint interpolation of e (npts = 4, 6, 8;
+    FAS correction with interp = npts)."""
+    e = _c(e)
+    uf = _c(uf).copy()
+    lib().or_prolong_add_lagrange(e.shape[0], int(npts), e, uf)
     return uf
 
 

@@ -231,3 +231,53 @@ def test_cubic_interpolation_properties(oracle):
                            inputs.sine_mode(nf)).max())
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(rates > 3.7), (errs, rates)
+
+
+# --------------------------------------------------------------------------
+# 6- and 8-point midpoint rules for the FAS correction (options interp = 6, 8)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("npts", [6, 8])
+def test_higher_order_midpoint_rules(oracle, npts):
+    """Even fine points take the coarse values; away from the boundary the
+    tensor-product npts-point rule reproduces polynomials of degree npts - 1
+    exactly (numpy polynomial evaluation); on sin(pi x) the error falls like
+    h^npts; the 4-point member of the family is the cubic rule."""
+    Nc = 15
+    Nf = 2 * Nc + 1
+    xc = np.arange(1, Nc + 1) / (Nc + 1)
+    xf = np.arange(1, Nf + 1) / (Nf + 1)
+    rng = np.random.default_rng(npts)
+    pc = rng.standard_normal(npts)  # degree npts - 1, coefficients low -> high
+    px = lambda x: np.polynomial.polynomial.polyval(x, pc)
+    py = lambda x: np.polynomial.polynomial.polyval(x, pc[::-1])
+    e = px(xc)[None, None, :] * py(xc)[None, :, None] * px(xc)[:, None, None]
+    out = oracle.prolong_add_lagrange(e, np.zeros((Nf, Nf, Nf)), npts)
+    ref = px(xf)[None, None, :] * py(xf)[None, :, None] * px(xf)[:, None, None]
+    inner = slice(npts - 1, Nf - npts + 1)  # stencils that stay inside the coarse grid
+    assert np.abs(out[inner, inner, inner] - ref[inner, inner, inner]).max() <= 1e-11 * np.abs(ref).max()
+    assert np.array_equal(out[1::2, 1::2, 1::2], e)
+    errs = []
+    for nc in (7, 15, 31):
+        nf = 2 * nc + 1
+        errs.append(np.abs(oracle.prolong_add_lagrange(inputs.sine_mode(nc), np.zeros((nf, nf, nf)),
+                                                       npts) - inputs.sine_mode(nf)).max())
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(rates > npts - 0.3), (errs, rates)
+    e4 = inputs.random_field(7, seed=9)
+    assert np.array_equal(oracle.prolong_add_lagrange(e4, np.zeros((15, 15, 15)), 4),
+                          oracle.prolong_add_cubic(e4, np.zeros((15, 15, 15))))
+
+
+def test_midpoint_rule_odd_extension_on_small_grids(oracle):
+    """On 1- and 3-point coarse lines the 6- and 8-point stencils reach past
+    both boundaries, on the 1-point line more than once.  With the odd
+    extension about both ends (the symmetry of every sine mode) the error on
+    sin(pi x) still falls with every order step (a zero extension makes it
+    grow from 4 to 8 points on the 3-point line)."""
+    for nc, factor in ((1, 1.8), (3, 5.0)):
+        nf = 2 * nc + 1
+        errs = [np.abs(oracle.prolong_add_lagrange(inputs.sine_mode(nc), np.zeros((nf, nf, nf)), n)
+                       - inputs.sine_mode(nf)).max() for n in (4, 6, 8)]
+        assert errs[0] > factor * errs[1] and errs[1] > factor * errs[2], (nc, errs)
+    assert errs[2] <= 5e-4
