@@ -614,7 +614,8 @@ def run_alpha(args):
         cp.close()
     return {"workload": "speedup model (Eq. pfasst_speedup) on one GB300: fine 127^3 wide M=5, "
                         "coarse 63^3 7-point M=3, dt=1/16, residual 1e-10"
-                        + ("; cubic interpolation of the coarse correction" if interp == 4 else ""),
+                        + ({4: "; cubic", 6: "; 6-point", 8: "; 8-point"}.get(interp, "")
+                           + (" interpolation of the coarse correction" if interp >= 4 else "")),
             "alpha": alpha, "beta": beta, "K_S": K_S, "t_fine_sweep_s": t_f,
             "t_coarse_sweep_s": t_c, "t_fas_s": t_r, "t_serial_sdc_16_steps_s": t_serial16,
             "pfasst": rows,
@@ -639,8 +640,9 @@ def main():
     ap.add_argument("--sweeps-fine", type=int, default=None,
                     help="override the fine sweeps per iteration")
     ap.add_argument("--iters", type=int, default=None, help="override the iteration cap")
-    ap.add_argument("--interp", type=int, default=None, choices=[2, 4],
-                    help="interpolation of the coarse correction: 2 trilinear, 4 cubic")
+    ap.add_argument("--interp", type=int, default=None, choices=[2, 4, 6, 8],
+                    help="interpolation of the coarse correction: 2 trilinear, 4 cubic, "
+                         "6 or 8 the 6- or 8-point midpoint rule")
     ap.add_argument("--mg-rel", type=float, default=None,
                     help="headline run: solver tolerance max(mg_tol, MG_REL x sweep residual)")
     ap.add_argument("--no-graphs", action="store_true", help="plain launches instead of CUDA graphs")
@@ -665,8 +667,10 @@ def main():
     if args.mg_rel:
         w = dict(w, mg_rel=args.mg_rel,
                  desc=w["desc"] + f"; solves stop at max(mg_tol, {args.mg_rel} x sweep residual)")
-    if args.interp == 4:
-        w = dict(w, interp=4, desc=w["desc"] + "; cubic interpolation of the coarse correction")
+    if args.interp and args.interp >= 4:
+        w = dict(w, interp=args.interp,
+                 desc=w["desc"] + ("; cubic" if args.interp == 4 else f"; {args.interp}-point")
+                 + " interpolation of the coarse correction")
     if args.persistent is not None:
         w = dict(w, persistent=args.persistent)
     if args.sweeps_fine:

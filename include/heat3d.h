@@ -118,8 +118,10 @@ typedef struct {
                                for testing) */
   int interp;               /* spatial interpolation of the coarse correction in the FAS
                                step (Sec. 1.1; the paper does not say which): 2 trilinear
-                               (default), 4 tensor-product cubic (4-point midpoint rule,
-                               odd reflection at the boundary) */
+                               (default); 4, 6, 8 the tensor-product 4-point (cubic),
+                               6- or 8-point Lagrange midpoint rule on the odd extension
+                               about the zero boundary.  With spatial coarsening the higher
+                               orders cut the MLSDC / PFASST iterations several-fold */
   int persistent;           /* multigrid solves as one persistent cooperative kernel each
                                (residual, all V-cycles and the stop rule in one launch, grid
                                barriers between the steps; bitwise the results of the launch

@@ -77,17 +77,18 @@ cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* e
                                long long ec_stride, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st);
 
-// uf += tensor-product cubic interpolation of ec (the FAS correction with
-// heat3d_config.interp = 4): along each axis even fine points take the
-// coarse value, odd ones (-e(I-1) + 9 e(I) + 9 e(I+1) - e(I+2)) / 16 with zero
-// boundary values and odd reflection beyond them.  FP64, B fields.  With
-// scratch t1, t2 (each at least Nf * Nf * Nc doubles per field, field stride
-// t_stride) it runs as three one-axis passes, bitwise the same, else as one
-// point-wise kernel.
-cudaError_t launch_prolong_add_cubic(const Grid& gc, const Grid& gf, int B, const double* ec,
-                                     long long ec_stride, double* uf, long long uf_stride,
-                                     cudaStream_t st, double* t1 = nullptr, double* t2 = nullptr,
-                                     long long t_stride = 0);
+// uf += tensor-product npts-point midpoint interpolation of ec (the FAS
+// correction with heat3d_config.interp = npts = 4, 6 or 8): along each axis
+// even fine points take the coarse value, odd ones the npts-point Lagrange
+// midpoint rule (4: (-e(I-1) + 9 e(I) + 9 e(I+1) - e(I+2)) / 16) on the odd
+// extension of the coarse line about its zero boundary values.  FP64, B
+// fields.  With scratch t1, t2 (each at least Nf * Nf * Nc doubles per field,
+// field stride t_stride) it runs as three one-axis passes, bitwise the same,
+// else as one point-wise kernel.
+cudaError_t launch_prolong_add_mid(int npts, const Grid& gc, const Grid& gf, int B,
+                                   const double* ec, long long ec_stride, double* uf,
+                                   long long uf_stride, cudaStream_t st, double* t1 = nullptr,
+                                   double* t2 = nullptr, long long t_stride = 0);
 
 // The whole V-cycle below (and including) a level with N <= 15, one block per
 // item, every level in shared memory (coarse_fused.cu).  Ns: sizes from that

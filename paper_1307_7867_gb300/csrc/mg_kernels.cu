@@ -198,30 +198,87 @@ __device__ __forceinline__ void cubic_taps(int f, int Nc, int (&ix)[4], double (
   }
 }
 
-// uf += P3 ec: one thread per fine point, separable sums x, then y, then z
-// (zero-weight taps are skipped).
-__global__ void k_prolong_cubic(Grid gc, Grid gf, const double* __restrict__ ec, long long ecs,
-                                double* __restrict__ uf, long long ufs) {
+// Taps of the 6- and 8-point midpoint rules, the Lagrange weights of equally
+// spaced points evaluated halfway between the middle two ((3, -25, 150, 150,
+// -25, 3) / 256 and (-5, 49, -245, 1225, 1225, -245, 49, -5) / 2048, exact in
+// binary): even 1-based fine points take their coarse point, odd ones the NT
+// coarse values around the midpoint on the odd extension of the coarse line
+// about both boundary points (period 2 (Nc + 1)), which also covers stencils
+// that reach past a boundary more than once on small grids.  Always NT taps
+// (unused ones weigh 0, index kept valid).
+template <int NT>
+__host__ __device__ __forceinline__ double mid_weight(int q) {
+  if (NT == 6) {
+    const double w6[6] = {3.0, -25.0, 150.0, 150.0, -25.0, 3.0};
+    return w6[q] / 256.0;
+  }
+  const double w8[8] = {-5.0, 49.0, -245.0, 1225.0, 1225.0, -245.0, 49.0, -5.0};
+  return w8[q] / 2048.0;
+}
+
+template <int NT>
+__host__ __device__ __forceinline__ void mid_taps(int f, int Nc, int (&ix)[NT], double (&w)[NT]) {
+  const int f1 = f + 1;
+  if ((f1 & 1) == 0) {
+#pragma unroll
+    for (int q = 0; q < NT; ++q) {
+      ix[q] = f1 / 2 - 1;
+      w[q] = q == 0 ? 1.0 : 0.0;
+    }
+    return;
+  }
+  const int I = (f1 - 1) / 2;  // the midpoint lies between coarse points I and I + 1 (1-based)
+  const int per = 2 * (Nc + 1);
+#pragma unroll
+  for (int q = 0; q < NT; ++q) {
+    double cw = mid_weight<NT>(q);
+    int r = (I - NT / 2 + 1 + q) % per;
+    if (r < 0) r += per;
+    int idx = r - 1;
+    if (r == 0 || r == Nc + 1) {
+      cw = 0.0;
+      idx = 0;
+    } else if (r > Nc + 1) {
+      cw = -cw;
+      idx = per - r - 1;
+    }
+    ix[q] = idx;
+    w[q] = cw;
+  }
+}
+
+// Taps of the NT-point rule (4: cubic_taps).
+template <int NT>
+__device__ __forceinline__ void interp_taps(int f, int Nc, int (&ix)[NT], double (&w)[NT]) {
+  if constexpr (NT == 4) cubic_taps(f, Nc, ix, w);
+  else mid_taps<NT>(f, Nc, ix, w);
+}
+
+// uf += P ec (NT-point midpoint rule per axis): one thread per fine point,
+// separable sums x, then y, then z (zero-weight taps are skipped).
+template <int NT>
+__global__ void k_prolong_mid(Grid gc, Grid gf, const double* __restrict__ ec, long long ecs,
+                              double* __restrict__ uf, long long ufs) {
   PointIdx p;
   if (!point_index(gf, p)) return;
-  int xi[4], yi[4], zi[4];
-  double xw[4], yw[4], zw[4];
-  cubic_taps(p.i, gc.N, xi, xw);
-  cubic_taps(p.j, gc.N, yi, yw);
-  cubic_taps(p.k, gc.N, zi, zw);
+  int xi[NT], yi[NT], zi[NT];
+  double xw[NT], yw[NT], zw[NT];
+  interp_taps<NT>(p.i, gc.N, xi, xw);
+  interp_taps<NT>(p.j, gc.N, yi, yw);
+  interp_taps<NT>(p.k, gc.N, zi, zw);
   const double* e = ec + p.b * ecs;
   double sz = 0.0;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
+  for (int c = 0; c < NT; ++c) {
     if (zw[c] == 0.0) continue;
     double sy = 0.0;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < NT; ++b) {
       if (yw[b] == 0.0) continue;
       const double* row = e + (long long)zi[c] * gc.plane + (long long)yi[b] * gc.px;
       double sx = 0.0;
 #pragma unroll
-      for (int a = 0; a < 4; ++a)
+      for (int a = 0; a < NT; ++a)
         if (xw[a] != 0.0) sx = fma(xw[a], __ldg(row + xi[a]), sx);
       sy = fma(yw[b], sx, sy);
     }
@@ -231,57 +288,60 @@ __global__ void k_prolong_cubic(Grid gc, Grid gf, const double* __restrict__ ec,
   *o = *o + sz;
 }
 
-// The same interpolation as k_prolong_cubic in three one-axis passes through
+// The same interpolation as k_prolong_mid in three one-axis passes through
 // dense temporaries (t1: [K][J][Nf], t2: [K][Nf][Nf] per item), with the sums
 // in the same order (x, then y, then z), so the result is bitwise the same
-// while each fine point costs a few fused multiply-adds instead of up to 64.
-__global__ void k_cubic_x(Grid gc, int Nf, const double* __restrict__ ec, long long ecs,
-                          double* __restrict__ t1, long long t1s) {
+// while each fine point costs a few fused multiply-adds instead of up to NT^3.
+template <int NT>
+__global__ void k_mid_x(Grid gc, int Nf, const double* __restrict__ ec, long long ecs,
+                        double* __restrict__ t1, long long t1s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // fine x
   const int J = blockIdx.y * blockDim.y + threadIdx.y;  // coarse y
   const int Nc = gc.N;
   const int b = blockIdx.z / Nc, K = blockIdx.z - b * Nc;
   if (i >= Nf || J >= Nc) return;
-  int xi[4];
-  double xw[4];
-  cubic_taps(i, Nc, xi, xw);
+  int xi[NT];
+  double xw[NT];
+  interp_taps<NT>(i, Nc, xi, xw);
   const double* row = ec + b * ecs + (long long)K * gc.plane + (long long)J * gc.px;
   double sx = 0.0;
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+  for (int a = 0; a < NT; ++a)
     if (xw[a] != 0.0) sx = fma(xw[a], __ldg(row + xi[a]), sx);
   t1[b * t1s + ((long long)K * Nc + J) * Nf + i] = sx;
 }
 
-__global__ void k_cubic_y(int Nc, int Nf, const double* __restrict__ t1, long long t1s,
-                          double* __restrict__ t2, long long t2s) {
+template <int NT>
+__global__ void k_mid_y(int Nc, int Nf, const double* __restrict__ t1, long long t1s,
+                        double* __restrict__ t2, long long t2s) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // fine x
   const int j = blockIdx.y * blockDim.y + threadIdx.y;  // fine y
   const int b = blockIdx.z / Nc, K = blockIdx.z - b * Nc;
   if (i >= Nf || j >= Nf) return;
-  int yi[4];
-  double yw[4];
-  cubic_taps(j, Nc, yi, yw);
+  int yi[NT];
+  double yw[NT];
+  interp_taps<NT>(j, Nc, yi, yw);
   const double* s = t1 + b * t1s + (long long)K * Nc * Nf + i;
   double sy = 0.0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < NT; ++q)
     if (yw[q] != 0.0) sy = fma(yw[q], s[(long long)yi[q] * Nf], sy);
   t2[b * t2s + ((long long)K * Nf + j) * Nf + i] = sy;
 }
 
-__global__ void k_cubic_z(Grid gf, int Nc, const double* __restrict__ t2, long long t2s,
-                          double* __restrict__ uf, long long ufs) {
+template <int NT>
+__global__ void k_mid_z(Grid gf, int Nc, const double* __restrict__ t2, long long t2s,
+                        double* __restrict__ uf, long long ufs) {
   PointIdx p;
   if (!point_index(gf, p)) return;
   const int Nf = gf.N;
-  int zi[4];
-  double zw[4];
-  cubic_taps(p.k, Nc, zi, zw);
+  int zi[NT];
+  double zw[NT];
+  interp_taps<NT>(p.k, Nc, zi, zw);
   const double* s = t2 + p.b * t2s + (long long)p.j * Nf + p.i;
   double sz = 0.0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
+  for (int q = 0; q < NT; ++q)
     if (zw[q] != 0.0) sz = fma(zw[q], s[(long long)zi[q] * Nf * Nf], sz);
   double* o = uf + p.b * ufs + p.idx;
   *o = *o + sz;
@@ -394,26 +454,39 @@ cudaError_t launch_mg_check(int B, const unsigned long long* norm_bits, int* act
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong_add_cubic(const Grid& gc, const Grid& gf, int B, const double* ec,
-                                     long long ec_stride, double* uf, long long uf_stride,
-                                     cudaStream_t st, double* t1, double* t2, long long t_stride) {
-  if (B <= 0) return cudaSuccess;
+template <int NT>
+static cudaError_t prolong_mid(const Grid& gc, const Grid& gf, int B, const double* ec,
+                               long long ec_stride, double* uf, long long uf_stride, cudaStream_t st,
+                               double* t1, double* t2, long long t_stride) {
   if (!t1 || !t2) {
-    k_prolong_cubic<<<point_grid(gf, B), dim3(32, 8), 0, st>>>(gc, gf, ec, ec_stride, uf, uf_stride);
+    k_prolong_mid<NT><<<point_grid(gf, B), dim3(32, 8), 0, st>>>(gc, gf, ec, ec_stride, uf, uf_stride);
     count_launch();
     return cudaGetLastError();
   }
   const int Nc = gc.N, Nf = gf.N;
   const dim3 blk(32, 8);
-  k_cubic_x<<<dim3((Nf + 31) / 32, (Nc + 7) / 8, Nc * B), blk, 0, st>>>(gc, Nf, ec, ec_stride, t1,
-                                                                         t_stride);
+  k_mid_x<NT><<<dim3((Nf + 31) / 32, (Nc + 7) / 8, Nc * B), blk, 0, st>>>(gc, Nf, ec, ec_stride, t1,
+                                                                           t_stride);
   count_launch();
-  k_cubic_y<<<dim3((Nf + 31) / 32, (Nf + 7) / 8, Nc * B), blk, 0, st>>>(Nc, Nf, t1, t_stride, t2,
-                                                                         t_stride);
+  k_mid_y<NT><<<dim3((Nf + 31) / 32, (Nf + 7) / 8, Nc * B), blk, 0, st>>>(Nc, Nf, t1, t_stride, t2,
+                                                                           t_stride);
   count_launch();
-  k_cubic_z<<<point_grid(gf, B), blk, 0, st>>>(gf, Nc, t2, t_stride, uf, uf_stride);
+  k_mid_z<NT><<<point_grid(gf, B), blk, 0, st>>>(gf, Nc, t2, t_stride, uf, uf_stride);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add_mid(int npts, const Grid& gc, const Grid& gf, int B,
+                                   const double* ec, long long ec_stride, double* uf,
+                                   long long uf_stride, cudaStream_t st, double* t1, double* t2,
+                                   long long t_stride) {
+  if (B <= 0) return cudaSuccess;
+  switch (npts) {
+    case 4: return prolong_mid<4>(gc, gf, B, ec, ec_stride, uf, uf_stride, st, t1, t2, t_stride);
+    case 6: return prolong_mid<6>(gc, gf, B, ec, ec_stride, uf, uf_stride, st, t1, t2, t_stride);
+    case 8: return prolong_mid<8>(gc, gf, B, ec, ec_stride, uf, uf_stride, st, t1, t2, t_stride);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <typename T>

@@ -194,8 +194,9 @@ static int validate(heat3d_ctx* c, const heat3d_config* cfg) {
     return h3d_fail(c, HEAT3D_EINVAL, "multigrid needs nu1 >= 1, nu2 >= 0, max_cycles >= 1");
   if (!(cfg->mg.rel >= 0 && cfg->mg.rel < 1))
     return h3d_fail(c, HEAT3D_EINVAL, "mg.rel must lie in [0, 1)");
-  if (cfg->interp != 0 && cfg->interp != 2 && cfg->interp != 4)
-    return h3d_fail(c, HEAT3D_EINVAL, "interp must be 2 (trilinear) or 4 (cubic)");
+  if (cfg->interp != 0 && cfg->interp != 2 && cfg->interp != 4 && cfg->interp != 6 &&
+      cfg->interp != 8)
+    return h3d_fail(c, HEAT3D_EINVAL, "interp must be 2 (trilinear), 4, 6 or 8 (midpoint rules)");
   if (cfg->persistent < -1 || cfg->persistent > 1)
     return h3d_fail(c, HEAT3D_EINVAL, "persistent must be -1 (automatic), 0 or 1");
   if (cfg->precision != HEAT3D_FP64 && cfg->precision != HEAT3D_MIXED)
@@ -1108,18 +1109,19 @@ int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
                       c->map_d, st));
   if (F.L.N == G.L.N) {
     CK(launch_update<double>(F.g, B * MF, D, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
-  } else if (c->cfg.interp == 4) {
+  } else if (c->cfg.interp >= 4) {
+    const int npts = c->cfg.interp;
     if (MF >= 3) {
       // separable passes node by node, temporaries in the fine integral
       // fields I (free between sweeps): fields 0 and 1 of each item
       const long long is = (long long)(MF - 1) * ff;
       double* I0 = F.I + (size_t)b0 * (MF - 1) * ff;
       for (int j = 0; j < MF; ++j)
-        CK(launch_prolong_add_cubic(G.g, F.g, B, D + (size_t)j * gf, (long long)MF * gf,
-                                    F.U + (size_t)b0 * MF * ff + (size_t)j * ff, (long long)MF * ff,
-                                    st, I0, I0 + ff, is));
+        CK(launch_prolong_add_mid(npts, G.g, F.g, B, D + (size_t)j * gf, (long long)MF * gf,
+                                  F.U + (size_t)b0 * MF * ff + (size_t)j * ff, (long long)MF * ff,
+                                  st, I0, I0 + ff, is));
     } else {
-      CK(launch_prolong_add_cubic(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
+      CK(launch_prolong_add_mid(npts, G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
     }
   } else {
     CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
