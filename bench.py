@@ -719,6 +719,13 @@ def main():
         out["cubic"] = run_variant(args, w, u0, uT, out, "fp64", 0.0, interp=4, tol_sdc=tol_c)
         out["cubic_mixed"] = run_variant(args, w, u0, uT, out, "mixed", 0.0, interp=4,
                                          tol_sdc=tol_c)
+        # 8-point interpolation of the coarse correction (interp = 8), run last;
+        # a failure is recorded in its entry and leaves the rest of the line intact
+        for key, prec in (("p8", "fp64"), ("p8_mixed", "mixed")):
+            try:
+                out[key] = run_variant(args, w, u0, uT, out, prec, 0.0, interp=8)
+            except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+                out[key] = {"precision": prec, "interp": 8, "error": str(exc)[:300]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         fv = st["vcycles_level"][0] / max(args.steps, 1)
