@@ -206,8 +206,9 @@ int heat3d_sdc_residual(heat3d_ctx* ctx, int level, int item, double* residual);
 /* FAS coupling of slots [begin, begin + count) (Sec. 1.1): restriction of
  * the fine state to the coarse level by injection in space and time, coarse
  * f^I and the FAS correction tau; and the interpolation of the coarse
- * correction back (trilinear in space, Lagrange in time) with f^I
- * re-evaluated on the fine level. */
+ * correction back (in space trilinear or the midpoint rule that
+ * heat3d_config.interp selects, in time Lagrange) with f^I re-evaluated on
+ * the fine level. */
 int heat3d_fas_restrict(heat3d_ctx* ctx, int begin, int count);
 int heat3d_fas_interpolate(heat3d_ctx* ctx, int begin, int count);
 
