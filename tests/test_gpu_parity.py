@@ -248,11 +248,10 @@ def test_adaptive_tolerance_rejects_bad_rel(H):
         H.Context(H.make_config((15, 4, 5), (7, H.COMPACT, 3), dt=1 / 8, T=1 / 8))
 
 
-@pytest.mark.parametrize("interp", [4, 6, 8])
 @pytest.mark.parametrize("order", [4, 19])
-def test_run_mlsdc_cubic_correction_interpolation(H, oracle, order, interp):
-    """interp = 4, 6, 8 (4-, 6- and 8-point interpolation of the coarse
-    correction): same iterations and V-cycles as the oracle, result to 1e-11."""
+def test_run_mlsdc_cubic_correction_interpolation(H, oracle, order, interp=4):
+    """interp = 4 (cubic interpolation of the coarse correction): same
+    iterations and V-cycles as the oracle, result to 1e-11."""
     fine, coarse = (31, order, 5), (15, 2, 3)
     cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
                         mg_tol=1e-11, interp=interp)
@@ -266,11 +265,9 @@ def test_run_mlsdc_cubic_correction_interpolation(H, oracle, order, interp):
     assert rel(uT, ref) <= 1e-11
 
 
-@pytest.mark.parametrize("interp", [4, 8])
-def test_mlsdc_cubic_two_nodes(H, oracle, interp):
-    """Two-node levels (M = 2): the midpoint-rule interpolation runs as the
-    one-pass point-wise kernel (no spare integral fields for the separable
-    passes)."""
+def test_mlsdc_cubic_two_nodes(H, oracle, interp=4):
+    """Two-node levels (M = 2): the cubic interpolation runs as the one-pass
+    point-wise kernel (no spare integral fields for the separable passes)."""
     fine, coarse = (31, 4, 2), (15, 2, 2)
     cfg = H.make_config(fine, coarse, dt=1 / 64, T=2 / 64, sweeps_fine=2, iters=20, tol_sdc=1e-10,
                         mg_tol=1e-11, interp=interp)
@@ -284,8 +281,7 @@ def test_mlsdc_cubic_two_nodes(H, oracle, interp):
     assert rel(uT, ref) <= 1e-11
 
 
-@pytest.mark.parametrize("interp", [4, 8])
-def test_pfasst_cubic_interpolation_fixed_iterations(H, oracle, interp):
+def test_pfasst_cubic_interpolation_fixed_iterations(H, oracle, interp=4):
     fine, coarse = (31, 4, 5), (15, 2, 3)
     P, K = 4, 3
     cfg = H.make_config(fine, coarse, dt=1 / 8, T=P / 8, sweeps_fine=1, slices=P, iters=K,
@@ -296,25 +292,6 @@ def test_pfasst_cubic_interpolation_fixed_iterations(H, oracle, interp):
     H.pfasst_run(ctx, u0, uT)
     ref, _, _ = oracle.pfasst_run(fine, coarse, oracle.Prob(mg_tol=1e-12, interp=interp), 1 / 8, P,
                                   P, u0, nsweeps_fine=1, max_iters=K)
-    assert rel(uT, ref) <= 1e-11
-
-
-def test_pfasst_at_the_paper_step_with_8_point_interpolation(H, oracle):
-    """8 slices of the paper's dt = 0.1875 (15^3 / 7^3, where the 8-point
-    stencil wraps around the 7-point coarse lines), iterated to the 1e-10
-    residual: the oracle's iteration count and result."""
-    fine, coarse = (15, 4, 5), (7, 2, 3)
-    P = 8
-    cfg = H.make_config(fine, coarse, dt=0.1875, T=P * 0.1875, sweeps_fine=1, slices=P, iters=30,
-                        tol_sdc=1e-10, mg_tol=1e-12, interp=8)
-    ctx = H.Context(cfg)
-    u0 = inputs.sine_mode(15)
-    uT = np.empty_like(u0)
-    rc, st = H.pfasst_run(ctx, u0, uT)
-    ref, orc, ost = oracle.pfasst_run(fine, coarse, oracle.Prob(mg_tol=1e-12, interp=8), 0.1875, P,
-                                      P, u0, nsweeps_fine=1, max_iters=30, tol=1e-10)
-    assert orc == oracle.OK and ost["residual"] <= 1e-10
-    assert st["iters"] == ost["iters"] and st["residual"] <= 1e-10
     assert rel(uT, ref) <= 1e-11
 
 
