@@ -30,11 +30,13 @@
  *   - SDC initial iterate: the initial value spread to every node;
  *   - FAS: injection in space and time, trilinear (or, with interp = 4, 6,
  *     8, the tensor-product 4-, 6- or 8-point midpoint rule) + Lagrange
- *     interpolation in time of the coarse correction; PFASST schedule and predictor as coded below (pinned by
- *     its converged limit, the serial collocation solution, and by the
- *     one-slice case equal to MLSDC; the iterates of a fixed iteration count
- *     in between follow this schedule reading and are "parity unpinned": no
- *     published iterate exists to compare them with);
+ *     interpolation in time of the coarse correction; PFASST schedule and
+ *     predictor as coded below, pinned by its converged limit (the serial
+ *     collocation solution), by the one-slice case equal to MLSDC, and at a
+ *     fixed iteration count by a scalar recursion of the same schedule on one
+ *     sine mode (both levels on one mesh, every node of every slice after 1-3
+ *     iterations) and by causality (slice 0 equals MLSDC's first step; the
+ *     first slices of a run equal a shorter run);
  *   - optional solver tolerance tied to the sweep's incoming residual
  *     (mg_rel), and the W-solve of the compact FAS restriction applied to the
  *     weighted residual (U_j - U_0 + W^{-1} r), see or_fas_restrict_st.
@@ -893,10 +895,11 @@ done:
  * the same serial coarse pass; interpolate; forward fine end values
  * (U^F[p][0] <- U^F[p-1][M-1]); residual = max over slices.  Stops when the
  * residual is <= tol (or after max_iters).  slice_res (nslices values or
- * NULL) receives the last per-slice residuals. */
+ * NULL) receives the last per-slice residuals; slice_nodes (nslices x M
+ * fields of N^3, or NULL) the fine node values U^F[p][m] of the last block. */
 int or_pfasst_run(const or_level* LF, const or_level* LG, const or_problem* P, double dt,
                   int nsteps, int nslices, const or_mlsdc_opts* o, const double* u0,
-                  double* uT, double* slice_res, or_stats* st) {
+                  double* uT, double* slice_res, double* slice_nodes, or_stats* st) {
   if (fas_check(LF, LG) != OR_OK || nslices < 1 || nsteps % nslices != 0) return OR_EINVAL;
   int MF = LF->M, MG = LG->M, PS = nslices, status = OR_OK;
   size_t nf = n3(LF->N), ng = n3(LG->N);
@@ -956,6 +959,7 @@ int or_pfasst_run(const or_level* LF, const or_level* LG, const or_problem* P, d
       if (o->tol >= 0 && r <= o->tol) break;
     }
     memcpy(ucur, UF + (PS - 1) * sf + (size_t)(MF - 1) * nf, nf * sizeof(double));
+    if (slice_nodes) memcpy(slice_nodes, UF, PS * sf * sizeof(double));
   }
   memcpy(uT, ucur, nf * sizeof(double));
 done:

@@ -101,7 +101,7 @@ def lib():
                                    P(Stats)]
         L.or_mlsdc_run.restype = I
         L.or_pfasst_run.argtypes = [P(Level), P(Level), P(Problem), D, I, I, P(MlsdcOpts), _dp,
-                                    _dp, C.c_void_p, P(Stats)]
+                                    _dp, C.c_void_p, C.c_void_p, P(Stats)]
         L.or_pfasst_run.restype = I
         _lib = L
     return _lib
@@ -338,10 +338,13 @@ def pfasst_run(fine, coarse, prob: Prob, dt, nsteps, nslices, u0, nsweeps_fine=1
     N = fine[0]
     uT = np.empty((N, N, N))
     sres = np.zeros(nslices)
+    snodes = np.zeros((nslices, fine[2], N, N, N))
     st = Stats()
     o = MlsdcOpts(nsweeps_fine, nsweeps_coarse, max_iters, tol, predictor)
     rc = lib().or_pfasst_run(C.byref(lf), C.byref(lg), C.byref(prob.c()), dt, nsteps, nslices,
-                             C.byref(o), _c(u0), uT, _ptr(sres), C.byref(st))
+                             C.byref(o), _c(u0), uT, _ptr(sres), _ptr(snodes), C.byref(st))
     d = st.as_dict()
     d["slice_residuals"] = sres
+    d["slice_nodes"] = snodes  # fine node values of every slice of the last block
+    d["slice_end"] = snodes[:, -1]
     return uT, rc, d
