@@ -8,7 +8,11 @@
  * (libheat3d.so) shares no code, header, table or constant generator with it.
  *
  * Everything is FP64 with straightforward loops, in the order the paper states
- * the method.  Grid functions are dense N^3 arrays of interior values,
+ * the method.  The per-point loops carry OpenMP pragmas: the parity oracle is
+ * built without OpenMP (one thread; the pragmas are ignored), and a second
+ * build with -fopenmp only times the CPU baseline on all host cores.  Every
+ * point is computed by the same expression in either build, so the two give
+ * bitwise equal results (tested); reductions stay serial.  Grid functions are dense N^3 arrays of interior values,
  * x fastest, z slowest; interior indices i, j, k run 1..N, h = 1/(N+1),
  * x_i = i*h, and u = 0 on the boundary (Sec. 1, Eqs. 1-2).
  *
@@ -82,6 +86,7 @@ typedef struct {
   long iters;      /* MLSDC / PFASST iterations */
   double residual; /* last SDC / PFASST residual computed */
   int notconv;     /* number of solves that hit the cycle cap */
+  double vcycle_points; /* sum over V-cycles of the solved grid's N^3 (work count) */
 } or_stats;
 
 static size_t n3(int N) { return (size_t)N * N * N; }
@@ -116,6 +121,7 @@ static double value_at(const double* u, int N, int i, int j, int k) {
  * 6 face neighbours) + (sum of the 12 edge neighbours)), zero boundary. */
 static void compact_laplacian(int N, const double* u, double* out) {
   double h = 1.0 / (N + 1);
+  #pragma omp parallel for
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j)
       for (int i = 1; i <= N; ++i) {
@@ -137,6 +143,7 @@ static void compact_laplacian(int N, const double* u, double* out) {
  * identity for the other stencils. */
 void or_weight(int N, int order, const double* u, double* out) {
   if (order != OR_COMPACT) { memcpy(out, u, n3(N) * sizeof(double)); return; }
+  #pragma omp parallel for
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j)
       for (int i = 1; i <= N; ++i) {
@@ -153,6 +160,7 @@ void or_weight(int N, int order, const double* u, double* out) {
 void or_laplacian(int N, int order, const double* u, double* out) {
   if (order == OR_COMPACT) { compact_laplacian(N, u, out); return; }
   double h = 1.0 / (N + 1);
+  #pragma omp parallel for
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j)
       for (int i = 1; i <= N; ++i) {
@@ -182,6 +190,7 @@ void or_apply_A(int N, int order, double c, const double* u, double* out) {
   double* w = (double*)malloc(n * sizeof(double));
   or_weight(N, order, u, w);
   or_laplacian(N, order, u, out);
+  #pragma omp parallel for
   for (size_t p = 0; p < n; ++p) out[p] = w[p] - c * out[p];
   free(w);
 }
@@ -190,6 +199,7 @@ void or_apply_A(int N, int order, double c, const double* u, double* out) {
 void or_residual(int N, int order, double c, const double* u, const double* b, double* r) {
   or_apply_A(N, order, c, u, r);
   size_t n = n3(N);
+  #pragma omp parallel for
   for (size_t p = 0; p < n; ++p) r[p] = b[p] - r[p];
 }
 
@@ -228,6 +238,7 @@ void or_jacobi(int N, int order, double c, const double* u, const double* b, dou
   double* r = (double*)malloc(n * sizeof(double));
   or_residual(N, order, c, u, b, r);
   double w = jacobi_omega(order), d = jacobi_diag(N, order, c);
+  #pragma omp parallel for
   for (size_t p = 0; p < n; ++p) out[p] = u[p] + w * r[p] / d;
   free(r);
 }
@@ -237,6 +248,7 @@ void or_jacobi(int N, int order, double c, const double* u, const double* b, dou
 void or_restrict_fw(int Nf, const double* r, double* bc) {
   int Nc = (Nf - 1) / 2;
   const double w[3] = {0.25, 0.5, 0.25};
+  #pragma omp parallel for
   for (int K = 1; K <= Nc; ++K)
     for (int J = 1; J <= Nc; ++J)
       for (int I = 1; I <= Nc; ++I) {
@@ -259,6 +271,7 @@ static double coarse_at(const double* e, int Nc, int I, int J, int K) {
  * take the mean of the two coarse neighbours along every odd axis. */
 void or_prolong_add(int Nc, const double* e, double* uf) {
   int Nf = 2 * Nc + 1;
+  #pragma omp parallel for
   for (int k = 1; k <= Nf; ++k)
     for (int j = 1; j <= Nf; ++j)
       for (int i = 1; i <= Nf; ++i) {
@@ -343,16 +356,19 @@ void or_prolong_add_lagrange(int Nc, int npts, const double* e, double* uf) {
   int Nf = 2 * Nc + 1;
   double* tx = (double*)malloc((size_t)Nf * Nc * Nc * sizeof(double));
   double* txy = (double*)malloc((size_t)Nf * Nf * Nc * sizeof(double));
+  #pragma omp parallel for
   for (int K = 0; K < Nc; ++K)
     for (int J = 0; J < Nc; ++J)
       for (int i = 1; i <= Nf; ++i)
         tx[((size_t)K * Nc + J) * Nf + (i - 1)] =
             line_at(e + ((size_t)K * Nc + J) * Nc, 1, Nc, i, npts);
+  #pragma omp parallel for
   for (int K = 0; K < Nc; ++K)
     for (int j = 1; j <= Nf; ++j)
       for (int i = 0; i < Nf; ++i)
         txy[((size_t)K * Nf + (j - 1)) * Nf + i] =
             line_at(tx + (size_t)K * Nc * Nf + i, Nf, Nc, j, npts);
+  #pragma omp parallel for
   for (int k = 1; k <= Nf; ++k)
     for (int j = 0; j < Nf; ++j)
       for (int i = 0; i < Nf; ++i)
@@ -497,6 +513,7 @@ static double lagrange_value(int M, const double* tau, int m, double s) {
 /* Phi(x) = sin(pi x1) sin(pi x2) sin(pi x3) at the interior points. */
 void or_phi(int N, double* phi) {
   double h = 1.0 / (N + 1);
+  #pragma omp parallel for
   for (int k = 1; k <= N; ++k)
     for (int j = 1; j <= N; ++j)
       for (int i = 1; i <= N; ++i)
@@ -518,6 +535,7 @@ static double forcing_g(const or_problem* P, double t) {
 static void eval_fI(const or_level* L, const or_problem* P, const double* u, double* F) {
   or_laplacian(L->N, L->order, u, F);
   size_t n = n3(L->N);
+  #pragma omp parallel for
   for (size_t p = 0; p < n; ++p) F[p] = P->nu * F[p];
 }
 
@@ -570,6 +588,7 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
     double tm = t0 + dt * tau[m], tm1 = t0 + dt * tau[m + 1];
     double dtm = dt * (tau[m + 1] - tau[m]);
     or_weight(N, L->order, U + m * n, wu);
+    #pragma omp parallel for
     for (size_t p = 0; p < n; ++p) {
       double fe_new = wphi[p] * forcing_g(P, tm); /* W f^E(U^{k+1}_m, t_m) */
       double fe_old = wphi[p] * forcing_g(P, tm); /* W f^E(U^k_m, t_m) */
@@ -587,7 +606,7 @@ int or_sdc_sweep(const or_level* L, const or_problem* P, double t0, double dt, d
                          P->nu1, P->nu2, &cyc, &res);
     if (rc == OR_ENOTCONV) { status = OR_ENOTCONV; if (st) st->notconv++; }
     else if (rc != OR_OK) { status = rc; break; }
-    if (st) { st->vcycles += cyc; st->solves += 1; }
+    if (st) { st->vcycles += cyc; st->solves += 1; st->vcycle_points += (double)cyc * n3(N); }
     eval_fI(L, P, U + (m + 1) * n, F + (m + 1) * n);
   }
   if (st) st->sweeps += 1;
@@ -730,6 +749,7 @@ int or_fas_restrict_st(const or_level* LF, const or_level* LG, const or_problem*
   or_eval_F_all(LG, P, UG, FG);
   for (int m = 0; m < MG; ++m) {
     int jm = node_map(MF, MG, m);
+    #pragma omp parallel for
     for (size_t p = 0; p < nf; ++p) {
       double q = 0.0;
       for (int j = 0; j < MF; ++j)
@@ -755,11 +775,12 @@ int or_fas_restrict_st(const or_level* LF, const or_level* LG, const or_problem*
                            &cyc, &res);
       if (rc == OR_ENOTCONV) { status = rc; if (st) st->notconv++; }
       else if (rc != OR_OK) { status = rc; free(wu0); free(wuj); break; }
-      if (st) { st->vcycles += cyc; st->solves += 1; }
+      if (st) { st->vcycles += cyc; st->solves += 1; st->vcycle_points += (double)cyc * nf; }
       for (size_t p = 0; p < nf; ++p) tmpf[p] = UF[(size_t)jm * nf + p] - UF[p] + xf[p];
       free(wu0); free(wuj);
     }
     inject(NF, NG, tmpf, tmpg);
+    #pragma omp parallel for
     for (size_t p = 0; p < ng; ++p) {
       double q = 0.0;
       for (int i = 0; i < MG; ++i)
@@ -790,6 +811,7 @@ int or_fas_interpolate(const or_level* LF, const or_level* LG, const or_problem*
   or_gl_nodes(MF, tf); or_gl_nodes(MG, tg);
   double* d = (double*)malloc(ng * sizeof(double));
   for (int j = 0; j < MF; ++j) {
+    #pragma omp parallel for
     for (size_t p = 0; p < ng; ++p) {
       double s = 0.0;
       for (int m = 0; m < MG; ++m)

@@ -19,19 +19,23 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "heat3d_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_heat3d.so")
+_LIB_OMP = os.path.join(_HERE, "liboracle_heat3d_omp.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV = 0, -1, -2, -3
 COMPACT = 19  # order code of the compact (Mehrstellen) 19-point stencil
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle with gcc: -O2, no FMA contraction, no fast-math.
+    omp=True builds the OpenMP variant (same source, per-point loops spread
+    over the host cores; bitwise the same results), used only for timing."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+                               *(["-fopenmp"] if omp else []), "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
 class Level(C.Structure):
@@ -46,7 +50,8 @@ class Problem(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("vcycles", C.c_long), ("solves", C.c_long), ("sweeps", C.c_long),
-                ("iters", C.c_long), ("residual", C.c_double), ("notconv", C.c_int)]
+                ("iters", C.c_long), ("residual", C.c_double), ("notconv", C.c_int),
+                ("vcycle_points", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -57,54 +62,73 @@ class MlsdcOpts(C.Structure):
                 ("tol", C.c_double), ("predictor", C.c_int)]
 
 
-_lib = None
+_libs = {}
+_use_omp = False
 _dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
 
 
+class openmp:
+    """Context manager: the wrappers below call the OpenMP build inside it."""
+
+    def __enter__(self):
+        global _use_omp
+        self.prev, _use_omp = _use_omp, True
+        return self
+
+    def __exit__(self, *exc):
+        global _use_omp
+        _use_omp = self.prev
+
+
 def lib():
-    global _lib
-    if _lib is None:
-        L = C.CDLL(build())
-        P, I, D = C.POINTER, C.c_int, C.c_double
-        L.or_laplacian.argtypes = [I, I, _dp, _dp]
-        L.or_weight.argtypes = [I, I, _dp, _dp]
-        L.or_apply_A.argtypes = [I, I, D, _dp, _dp]
-        L.or_residual.argtypes = [I, I, D, _dp, _dp, _dp]
-        L.or_jacobi.argtypes = [I, I, D, _dp, _dp, _dp]
-        L.or_restrict_fw.argtypes = [I, _dp, _dp]
-        L.or_prolong_add.argtypes = [I, _dp, _dp]
-        L.or_prolong_add_cubic.argtypes = [I, _dp, _dp]
-        L.or_prolong_add_lagrange.argtypes = [I, I, _dp, _dp]
-        L.or_vcycle.argtypes = [I, I, D, _dp, _dp, I, I]
-        L.or_mg_solve.argtypes = [I, I, D, _dp, _dp, D, I, I, I, P(I), P(D)]
-        L.or_mg_solve.restype = I
-        L.or_gl_nodes.argtypes = [I, _dp]
-        L.or_qmatrix.argtypes = [I, _dp]
-        L.or_smatrix.argtypes = [I, _dp]
-        L.or_phi.argtypes = [I, _dp]
-        L.or_maxabs.argtypes = [C.c_size_t, _dp]
-        L.or_maxabs.restype = D
-        L.or_eval_F_all.argtypes = [P(Level), P(Problem), _dp, _dp]
-        L.or_spread.argtypes = [P(Level), P(Problem), _dp, _dp, _dp]
-        L.or_sdc_sweep.argtypes = [P(Level), P(Problem), D, D, _dp, _dp, C.c_void_p, P(Stats)]
-        L.or_sdc_sweep.restype = I
-        L.or_sdc_residual.argtypes = [P(Level), P(Problem), D, D, _dp, _dp, C.c_void_p]
-        L.or_sdc_residual.restype = D
-        L.or_sdc_run.argtypes = [P(Level), P(Problem), D, I, I, D, _dp, _dp, P(Stats)]
-        L.or_sdc_run.restype = I
-        L.or_fas_restrict.argtypes = [P(Level), P(Level), P(Problem), D, D, _dp, _dp, _dp, _dp,
-                                      _dp, _dp]
-        L.or_fas_restrict.restype = I
-        L.or_fas_interpolate.argtypes = [P(Level), P(Level), P(Problem), _dp, _dp, _dp, _dp]
-        L.or_fas_interpolate.restype = I
-        L.or_mlsdc_run.argtypes = [P(Level), P(Level), P(Problem), D, I, P(MlsdcOpts), _dp, _dp,
-                                   P(Stats)]
-        L.or_mlsdc_run.restype = I
-        L.or_pfasst_run.argtypes = [P(Level), P(Level), P(Problem), D, I, I, P(MlsdcOpts), _dp,
-                                    _dp, C.c_void_p, C.c_void_p, P(Stats)]
-        L.or_pfasst_run.restype = I
-        _lib = L
-    return _lib
+    L = _libs.get(_use_omp)
+    if L is None:
+        L = _load(_use_omp)
+        _libs[_use_omp] = L
+    return L
+
+
+def _load(omp):
+    L = C.CDLL(build(omp=omp))
+    P, I, D = C.POINTER, C.c_int, C.c_double
+    L.or_laplacian.argtypes = [I, I, _dp, _dp]
+    L.or_weight.argtypes = [I, I, _dp, _dp]
+    L.or_apply_A.argtypes = [I, I, D, _dp, _dp]
+    L.or_residual.argtypes = [I, I, D, _dp, _dp, _dp]
+    L.or_jacobi.argtypes = [I, I, D, _dp, _dp, _dp]
+    L.or_restrict_fw.argtypes = [I, _dp, _dp]
+    L.or_prolong_add.argtypes = [I, _dp, _dp]
+    L.or_prolong_add_cubic.argtypes = [I, _dp, _dp]
+    L.or_prolong_add_lagrange.argtypes = [I, I, _dp, _dp]
+    L.or_vcycle.argtypes = [I, I, D, _dp, _dp, I, I]
+    L.or_mg_solve.argtypes = [I, I, D, _dp, _dp, D, I, I, I, P(I), P(D)]
+    L.or_mg_solve.restype = I
+    L.or_gl_nodes.argtypes = [I, _dp]
+    L.or_qmatrix.argtypes = [I, _dp]
+    L.or_smatrix.argtypes = [I, _dp]
+    L.or_phi.argtypes = [I, _dp]
+    L.or_maxabs.argtypes = [C.c_size_t, _dp]
+    L.or_maxabs.restype = D
+    L.or_eval_F_all.argtypes = [P(Level), P(Problem), _dp, _dp]
+    L.or_spread.argtypes = [P(Level), P(Problem), _dp, _dp, _dp]
+    L.or_sdc_sweep.argtypes = [P(Level), P(Problem), D, D, _dp, _dp, C.c_void_p, P(Stats)]
+    L.or_sdc_sweep.restype = I
+    L.or_sdc_residual.argtypes = [P(Level), P(Problem), D, D, _dp, _dp, C.c_void_p]
+    L.or_sdc_residual.restype = D
+    L.or_sdc_run.argtypes = [P(Level), P(Problem), D, I, I, D, _dp, _dp, P(Stats)]
+    L.or_sdc_run.restype = I
+    L.or_fas_restrict.argtypes = [P(Level), P(Level), P(Problem), D, D, _dp, _dp, _dp, _dp,
+                                  _dp, _dp]
+    L.or_fas_restrict.restype = I
+    L.or_fas_interpolate.argtypes = [P(Level), P(Level), P(Problem), _dp, _dp, _dp, _dp]
+    L.or_fas_interpolate.restype = I
+    L.or_mlsdc_run.argtypes = [P(Level), P(Level), P(Problem), D, I, P(MlsdcOpts), _dp, _dp,
+                               P(Stats)]
+    L.or_mlsdc_run.restype = I
+    L.or_pfasst_run.argtypes = [P(Level), P(Level), P(Problem), D, I, I, P(MlsdcOpts), _dp,
+                                _dp, C.c_void_p, C.c_void_p, P(Stats)]
+    L.or_pfasst_run.restype = I
+    return L
 
 
 def _c(a):
