@@ -21,6 +21,7 @@ bounded sample of the same workload instead.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -34,12 +35,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
-
-# Fine-level V-cycles per MLSDC step of the default workload, counted on a
-# full GB300 run (the oracle performs the same cycles: the parity tests check
-# equal counts).  Used only by --impl reference to scale its timed sample.
-REF_FINE_VCYCLES_PER_STEP = 596.0
-REF_COARSE_VCYCLES_PER_STEP = 164.0
 
 # DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
 # capture of the kernel as it is now (profiles/stencils_fine_255_*.md); key:
@@ -62,9 +57,11 @@ WORKLOADS = {
         iters=0, tol_sdc=-1.0, mg_tol=1e-10, precision="fp64", steps=8, warmup=3),
     "c3": dict(
         desc="PFASST, 16 slices batched, fine 127^3 wide M=5 / coarse 63^3 7-point M=3, "
-             "dt=1/16, 5 iterations, 1 fine sweep per iteration",
+             "dt=1/16, 5 iterations, 1 fine sweep per iteration; coarse-level solves as one "
+             "persistent kernel each, fine-level V-cycles replayed from CUDA graphs",
         fine=(127, 4, 5), coarse=(63, 2, 3), dt=1 / 16, sweeps_fine=1, sweeps_coarse=1,
-        slices=16, iters=5, tol_sdc=-1.0, mg_tol=1e-11, precision="fp64", steps=16, warmup=16),
+        slices=16, iters=5, tol_sdc=-1.0, mg_tol=1e-11, precision="fp64", steps=16, warmup=16,
+        persistent=1),
     "paper": dict(
         desc="the paper's setup with the wide fine stencil: PFASST on 32 slices of dt=0.1875 "
              "(T=6), fine 255^3 wide M=5 / coarse 127^3 7-point M=3, 1 fine sweep per "
@@ -87,7 +84,7 @@ WORKLOADS = {
         desc="mixed precision, fine 511^3 wide M=5 / coarse 255^3 7-point M=3, dt=1/32, "
              "MLSDC to residual 1e-10, FP32 V-cycles in FP64 refinement to 1e-11",
         fine=(511, 4, 5), coarse=(255, 2, 3), dt=1 / 32, sweeps_fine=2, sweeps_coarse=1,
-        slices=1, iters=20, tol_sdc=1e-10, mg_tol=1e-11, precision="mixed", steps=2, warmup=1),
+        slices=1, iters=20, tol_sdc=1e-10, mg_tol=1e-11, precision="mixed", steps=2, warmup=3),
 }
 
 
@@ -392,8 +389,55 @@ def run_variant(args, w, u0, uT, out, precision, mg_rel, interp=None, tol_sdc=No
             "equal_error": err_m <= 1.01 * out["accuracy"]["rel_err_vs_pde_solution"]}
 
 
-def oracle_sample_fine_vcycle(w):
-    """Seconds per fine V-cycle (with its residual check) of the oracle at full size."""
+def run_config(args, name, precision=None, interp=None):
+    """Another configuration of the scope table measured in the same process as
+    the headline (its own context, warm-up, timed steps, clocks and roofline);
+    returns the fields of its own bench line."""
+    import copy
+    w = dict(WORKLOADS[name])
+    if precision and precision != w["precision"]:
+        w = dict(w, precision=precision, desc=w["desc"] + "; FP32 V-cycles in FP64 refinement")
+    if interp:
+        w = dict(w, interp=interp, desc=w["desc"] + f"; {interp}-point interpolation of the "
+                                                    "coarse correction")
+    a = copy.copy(args)
+    a.steps, a.warmup, a.no_e2e = w["steps"], w["warmup"], name == "c4"
+    out, ctx, st, _, _ = run_ours(a, w, 0, 1)
+    ctx.close()
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "stats",
+            "accuracy", "roofline", "e2e", "gpu_launches", "clocks")
+    return {k: out[k] for k in keep if out.get(k) is not None}
+
+
+def host_info():
+    """Threads this process may use and the host CPU model."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return cores, f"{model or 'unknown'} ({platform.machine()})"
+
+
+def oracle_sample_fine_vcycle(w, omp=False):
+    """Seconds per fine V(2,1) cycle (with its residual check) of the oracle at full size."""
     from oracle import oracle as O
     from paper_1307_7867_gb300 import inputs
     Nf, order, M = w["fine"]
@@ -401,38 +445,112 @@ def oracle_sample_fine_vcycle(w):
     c = w["dt"] * tau1 * 0.1
     b = inputs.sine_mode(Nf)
     u = np.zeros_like(b)
-    t0 = time.perf_counter()
-    O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=1)
-    t1 = time.perf_counter()
-    O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=2)
-    t2 = time.perf_counter()
+    with (O.openmp() if omp else contextlib.nullcontext()):
+        t0 = time.perf_counter()
+        O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=1)
+        t1 = time.perf_counter()
+        O.mg_solve(u, b, order, c, tol=-1.0, max_cycles=2)
+        t2 = time.perf_counter()
     return (t2 - t1) - (t1 - t0), (t2 - t0)
 
 
-def cpu_baseline(w, fine_v, coarse_v, sample_desc_extra=""):
-    per_v, spent = oracle_sample_fine_vcycle(w)
-    t_step = per_v * (fine_v + coarse_v / 8.0)
+def oracle_sample_iteration_rest(w, omp=True):
+    """Seconds of one MLSDC iteration (one SDC sweep for a single level) of the
+    oracle at full size with every multigrid solve capped at zero cycles: the
+    substep right-hand sides, quadrature, operator refreshes, FAS restriction
+    and tau, the coarse sweep, the interpolation and the residuals, plus the
+    residual check each solve starts with."""
+    from oracle import oracle as O
+    from paper_1307_7867_gb300 import inputs
+    prob = O.Prob(nu=0.1, forcing=1, kappa=1.0, mg_tol=w["mg_tol"], mg_max=0,
+                  interp=w.get("interp", 2))
+    u0 = inputs.sine_mode(w["fine"][0])
+    with (O.openmp() if omp else contextlib.nullcontext()):
+        t0 = time.perf_counter()
+        if w["coarse"]:
+            O.mlsdc_run(w["fine"], w["coarse"], prob, w["dt"], 1, u0,
+                        nsweeps_fine=w["sweeps_fine"], nsweeps_coarse=w["sweeps_coarse"],
+                        max_iters=1, tol=-1.0, predictor=0)
+        else:
+            O.sdc_run(*w["fine"], prob, w["dt"], 1, 1, u0)
+        return time.perf_counter() - t0
+
+
+def oracle_step_model(w, iters, vpoints, single_thread=True):
+    """Oracle seconds per time step on this host: iters x (one iteration's
+    non-solve work) + (V-cycle work / N_fine^3) x (seconds per fine V-cycle),
+    timed with the OpenMP build on all host cores and, for the fine V-cycle,
+    with the single-thread parity build too."""
+    from oracle import oracle as O
+    cores, model = host_info()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    try:
+        O.build(omp=True)
+        omp = True
+    except Exception:  # no OpenMP compiler support: one thread only
+        omp, cores = False, 1
     Nf = w["fine"][0]
-    return {"value": Nf ** 3 / t_step, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle (single-thread C, FP64) timed for 1 and 2 V(2,1) cycles of a fine "
-                       f"{Nf}^3 solve ({spent:.1f} s); per step = seconds per fine V-cycle x "
-                       f"({fine_v:.0f} fine + {coarse_v:.0f}/8 coarse V-cycles per step)"
-                       f"{sample_desc_extra}; quadrature, FAS and transfer work excluded, "
-                       f"so the CPU figure is optimistic")}
+    tv_all, _ = oracle_sample_fine_vcycle(w, omp=omp)
+    tx_all = oracle_sample_iteration_rest(w, omp=omp)
+    fine_equiv = vpoints / float(Nf) ** 3
+    step_all = iters * tx_all + fine_equiv * tv_all
+    out = {"cores": cores, "cpu_model": model, "t_step_all_cores": step_all,
+           "t_fine_vcycle_all_cores": tv_all, "t_iteration_rest_all_cores": tx_all,
+           "iters_per_step": iters, "fine_vcycles_equiv_per_step": fine_equiv}
+    if single_thread:
+        tv_1, _ = oracle_sample_fine_vcycle(w, omp=False)
+        out["t_fine_vcycle_1_thread"] = tv_1
+        # the iteration's remaining work scaled by the V-cycle's thread speed-up
+        out["t_step_1_thread"] = iters * tx_all * (tv_1 / tv_all) + fine_equiv * tv_1
+    return out
 
 
-def run_reference(args, w):
-    """The oracle on this machine's host cores: each step is one fine V-cycle at full size,
-    scaled to grid-pt-steps/s by the V-cycles one step of this workload performs."""
+def cpu_baseline(w, iters, vpoints, counts_from):
+    m = oracle_step_model(w, iters, vpoints)
+    Nf = w["fine"][0]
+    return {"value": Nf ** 3 / m["t_step_all_cores"], "unit": "grid-pt-steps/s",
+            "cores": m["cores"], "kind": "oracle", "cpu_model": m["cpu_model"],
+            "single_thread_value": Nf ** 3 / m["t_step_1_thread"],
+            "sample": (f"oracle (plain C, FP64) at full size on this host: one fine V(2,1) cycle "
+                       f"({m['t_fine_vcycle_all_cores']:.2f} s on {m['cores']} threads, "
+                       f"{m['t_fine_vcycle_1_thread']:.2f} s on one) and one MLSDC iteration with "
+                       f"its solves capped at zero cycles ({m['t_iteration_rest_all_cores']:.2f} s: "
+                       f"sweeps' right-hand sides and quadrature, FAS, coarse sweep, "
+                       f"interpolation, residuals); per step = {iters:.2f} iterations x that + "
+                       f"{m['fine_vcycles_equiv_per_step']:.1f} fine-V-cycle equivalents "
+                       f"(sum of V-cycles x N^3 / N_fine^3) x the V-cycle, counts per step "
+                       f"{counts_from}; single-thread value scales the iteration's remaining "
+                       f"work by the V-cycle's thread speed-up"),
+            "model": m}
+
+
+def stored_step_counts(name):
+    """The oracle's own iterations and V-cycle work per step (oracle/step_counts.json)."""
+    p = os.path.join(ROOT, "oracle", "step_counts.json")
+    try:
+        return json.load(open(p))[name]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def run_reference(args, w, name):
+    """The oracle on this machine's host cores: each step times one fine V-cycle and
+    one iteration's remaining work at full size (OpenMP build, all cores) and
+    scales them by the oracle's own counts per step of this workload."""
     from oracle import oracle as O
     O.build()
-    times = []
+    counts = stored_step_counts(name)
+    if counts is None:
+        return {"impl": "reference", "unavailable": f"no stored oracle step counts for workload "
+                                                    f"{name} (oracle/step_counts.py)"}
+    iters, vpts = counts["iters_per_step"], counts["vcycle_points_per_step"]
+    times, last = [], None
     for s in range(args.warmup + args.steps):
-        per_v, _ = oracle_sample_fine_vcycle(w)
+        last = oracle_step_model(w, iters, vpts, single_thread=False)
         if s >= args.warmup:
-            times.append(per_v)
-    per_v = sum(times) / len(times)
-    t_step = per_v * (REF_FINE_VCYCLES_PER_STEP + REF_COARSE_VCYCLES_PER_STEP / 8.0)
+            times.append(last["t_step_all_cores"])
+    t_step = sum(times) / len(times)
+    one = oracle_step_model(w, iters, vpts, single_thread=True)
     Nf = w["fine"][0]
     v = Nf ** 3 / t_step
     return {"impl": "reference", "metric": "grid-pt-steps/s at fixed error", "value": v,
@@ -440,10 +558,16 @@ def run_reference(args, w):
             "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(w, 1),
-            "cpu_baseline": {"value": v, "unit": "grid-pt-steps/s", "cores": 1, "kind": "oracle",
-                             "sample": "per step: one fine V(2,1) cycle of the oracle at full size, "
-                                       f"scaled by {REF_FINE_VCYCLES_PER_STEP:.0f} fine + "
-                                       f"{REF_COARSE_VCYCLES_PER_STEP:.0f}/8 coarse V-cycles per step"},
+            "cpu_baseline": {"value": v, "unit": "grid-pt-steps/s", "cores": last["cores"],
+                             "kind": "oracle", "cpu_model": last["cpu_model"],
+                             "single_thread_value": Nf ** 3 / one["t_step_1_thread"],
+                             "sample": f"per step: one fine V(2,1) cycle and one MLSDC iteration "
+                                       f"with solves capped at zero cycles, oracle at full size "
+                                       f"on {last['cores']} threads, scaled by the oracle's own "
+                                       f"counts for this workload ({iters:.2f} iterations, "
+                                       f"{vpts / float(Nf) ** 3:.1f} fine-V-cycle equivalents per "
+                                       f"step over its first {counts['steps']} steps, "
+                                       f"oracle/step_counts.json)"},
             "e2e": {"value": v, "unit": "grid-pt-steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -532,10 +656,12 @@ def run_serving(args):
     warm = inputs.request_stream(3, rate=0.0, seed=99, sizes=(63, 127, 255), horizons=(0.25,))
     serve(warm, 0.0)  # builds every group's kernels, graphs and tuning once
     sat_reqs = inputs.request_stream(n, rate=0.0, seed=1307)
-    sat = serve(sat_reqs, 0.0)
+    with ClockSampler(torch.cuda.current_device()) as clk_sat:
+        sat = serve(sat_reqs, 0.0)
     rate = 0.7 * n / sat["makespan_s"]
     load_reqs = inputs.request_stream(n, rate=rate, seed=1307)
-    lo = serve(load_reqs, rate)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        lo = serve(load_reqs, rate)
     # the same requests give the same results whatever else was in the batch
     same = all(np.array_equal(a[0], b[0]) for a, b in zip(sat["outs"], lo["outs"]))
     return {"metric": "grid-pt-steps/s at fixed error", "value": lo["value"],
@@ -550,8 +676,9 @@ def run_serving(args):
                        "requests": n, "arrival_rate_rps": rate},
             "latency": {"p50_s": lo["p50_s"], "p99_s": lo["p99_s"], "completed": lo["completed"]},
             "saturation": {"value": sat["value"], "makespan_s": sat["makespan_s"],
-                           "p50_s": sat["p50_s"], "p99_s": sat["p99_s"]},
-            "results_independent_of_batch": same}
+                           "p50_s": sat["p50_s"], "p99_s": sat["p99_s"],
+                           "clocks": clk_sat.summary()},
+            "results_independent_of_batch": same, "clocks": clk.summary()}
 
 
 def run_alpha(args):
@@ -576,6 +703,8 @@ def run_alpha(args):
                             use_graphs=1, autotune=1, interp=interp)
         return H.Context(cfg, stream=st_)
 
+    clk = ClockSampler(torch.cuda.current_device())
+    clk.__enter__()
     # alpha and beta from single-slice sweeps on a representative state
     c = ctx_for(1)
     H.heat3d_set_state(c, 0, 0, 0.0, u0)
@@ -612,13 +741,14 @@ def run_alpha(args):
         rows.append({"P": P, "K_P": K_P, "seconds": t_p, "speedup_model": model,
                      "speedup_measured": measured, "residual": sp["residual"]})
         cp.close()
+    clk.__exit__()
     return {"workload": "speedup model (Eq. pfasst_speedup) on one GB300: fine 127^3 wide M=5, "
                         "coarse 63^3 7-point M=3, dt=1/16, residual 1e-10"
                         + ({4: "; cubic", 6: "; 6-point", 8: "; 8-point"}.get(interp, "")
                            + (" interpolation of the coarse correction" if interp >= 4 else "")),
             "alpha": alpha, "beta": beta, "K_S": K_S, "t_fine_sweep_s": t_f,
             "t_coarse_sweep_s": t_c, "t_fas_s": t_r, "t_serial_sdc_16_steps_s": t_serial16,
-            "pfasst": rows,
+            "pfasst": rows, "clocks": clk.summary(),
             "paper_alpha": {"bgq_small": 0.083, "bgq_large": 0.36, "xe6_small": 0.086,
                             "xe6_large": 0.4}}
 
@@ -650,6 +780,8 @@ def main():
                     help="multigrid solves as one persistent kernel: -1 on grids N <= 31 "
                          "(default), 0 never, 1 on grids N <= 63")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end pass")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="default workload: skip the c3, c4 and c5 entries")
     ap.add_argument("--profile-step", choices=["fp64", "mixed"], default=None,
                     help="profiling case: one step of the workload capped at one iteration")
     ap.add_argument("--kernel-case", choices=["fp64", "mixed"], default=None,
@@ -698,7 +830,7 @@ def main():
 
     if args.impl == "reference":
         if rank == 0:
-            print(json.dumps(run_reference(args, w)), flush=True)
+            print(json.dumps(run_reference(args, w, args.workload)), flush=True)
         return
 
     if world > 1:
@@ -727,10 +859,31 @@ def main():
             except Exception as exc:  # noqa: BLE001 - reported in the JSON line
                 out[key] = {"precision": prec, "interp": 8, "error": str(exc)[:300]}
 
+    if rank == 0 and world == 1 and not args.no_configs and args.workload == "c2":
+        # the other configurations of the scope table, each with its own
+        # timed region, clocks and roofline; a failure is recorded in its entry
+        for key, name, prec, interp in (("c3", "c3", None, None), ("c3_mixed", "c3", "mixed", None),
+                                        ("c3_p8", "c3", None, 8), ("c3_p8_mixed", "c3", "mixed", 8),
+                                        ("c4", "c4", None, None)):
+            try:
+                out[key] = run_config(args, name, prec, interp)
+            except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+                out[key] = {"error": str(exc)[:300]}
+        try:
+            c5 = run_serving(args)
+            out["c5"] = {k: c5[k] for k in ("value", "unit", "ms_per_step", "config", "latency",
+                                            "saturation", "results_independent_of_batch",
+                                            "clocks")}
+        except Exception as exc:  # noqa: BLE001
+            out["c5"] = {"error": str(exc)[:300]}
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        fv = st["vcycles_level"][0] / max(args.steps, 1)
-        cv = st["vcycles_level"][1] / max(args.steps, 1)
-        out["cpu_baseline"] = cpu_baseline(w, fv, cv)
+        K = max(args.steps, 1)
+        Ng = w["coarse"][0] if w["coarse"] else 0
+        vpts = (st["vcycles_level"][0] * float(w["fine"][0]) ** 3
+                + st["vcycles_level"][1] * float(Ng) ** 3) / K
+        iters = st["iters"] / K if w["coarse"] else st["sweeps"] / K
+        out["cpu_baseline"] = cpu_baseline(w, iters, vpts, "counted by this GPU run")
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
