@@ -2,17 +2,21 @@
 // solves (zero forcing, 3-node SDC, 7-point Laplacian, fixed sweeps per step).
 //
 // Requests are grouped by grid size N.  A group owns one heat3d context whose
-// item slots hold the requests resident on the device; its workspace, plus
-// one pitched "current value" field per slot and the initial-value tables,
-// come from the caller's device pool through a first-fit sub-allocator.  A
-// request is admitted when its group has a free slot and (for a new group)
-// the pool has room; otherwise it waits in arrival order.  One scheduler
-// thread advances every group by one time step per round: the group's
-// resident requests are packed into items 0..A-1, swept together (per-item
-// nu, dt, forcing data, multigrid masks), and unpacked.  A request whose last
-// step is done is copied to host memory, its slot freed at once, and new
-// requests join the next round.  Each item's arithmetic depends only on its
-// own data, so a result is the same alone or in any mix.
+// item slots hold the requests resident on the device, its own CUDA stream
+// and its own stepping thread; its workspace, plus one pitched "current
+// value" field per slot and the initial-value tables, come from the caller's
+// device pool through a first-fit sub-allocator.  The admission thread hands
+// a request to its group when the group has a free slot and (for a new group)
+// the pool has room; otherwise the request waits in arrival order.  Each
+// group thread advances its group by one time step per round: requests handed
+// over since the last round get their initial values, the resident requests
+// are packed into items 0..A-1, swept together (per-item nu, dt, forcing
+// data, multigrid masks) and unpacked.  A request whose last step is done is
+// copied to host memory and its slot freed at once; a waiting request takes
+// it in the next round.  Groups of different sizes run on their own streams
+// from their own threads, so their kernels overlap on the device and a small
+// request does not wait behind a large one's step.  Each item's arithmetic
+// depends only on its own data, so a result is the same alone or in any mix.
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
@@ -69,11 +73,6 @@ struct Pool {
   void release(char* p) {
     if (p) used.erase((size_t)(p - base));
   }
-  size_t free_bytes() const {
-    size_t u = 0;
-    for (auto& kv : used) u += kv.second;
-    return bytes - u;
-  }
 };
 
 struct Req {
@@ -90,11 +89,18 @@ struct Req {
 struct Group {
   int N = 0;
   heat3d_ctx* ctx = nullptr;
+  cudaStream_t st = nullptr;
   char* chunk = nullptr;
   double* ucur = nullptr;  // [slot] pitched fields
   double* tab = nullptr;   // 3 * N * kModes doubles
   double* amp = nullptr;   // kModes doubles
-  std::vector<std::shared_ptr<Req>> slots;
+  std::vector<std::shared_ptr<Req>> slots;  // the group thread's own
+  // guarded by the server mutex:
+  std::deque<std::shared_ptr<Req>> incoming;  // handed over, not yet started
+  int reserved = 0;                           // residents + incoming
+  bool stop = false;
+  std::condition_variable cv;  // wakes the group thread
+  std::thread th;
   int active() const {
     int a = 0;
     for (auto& s : slots) a += s != nullptr;
@@ -111,15 +117,15 @@ double now_s() {
 
 struct heat3d_server {
   heat3d_server_config cfg{};
-  cudaStream_t st = nullptr;
-  Pool pool;
+  Pool pool;  // the admission thread's own
   std::mutex mu;
   std::condition_variable cv_submit, cv_done;
   std::deque<std::shared_ptr<Req>> pending;
   std::map<uint64_t, std::shared_ptr<Req>> all;
-  std::map<int, std::unique_ptr<Group>> groups;
+  std::map<int, std::unique_ptr<Group>> groups;  // created and released by the admission thread
   std::vector<double> latencies;
   uint64_t next_ticket = 1;
+  uint64_t freed = 0;  // counts slot releases, so that waiting requests are retried
   bool stop = false;
   std::thread worker;
   char err[512] = {0};
@@ -130,7 +136,7 @@ static int srv_fail(heat3d_server* s, int code, const char* msg) {
   return code;
 }
 
-static heat3d_config group_config(const heat3d_server* s, int N) {
+static heat3d_config group_config(const heat3d_server* s, int N, cudaStream_t st) {
   heat3d_config c;
   heat3d_config_default(&c);
   c.nlevels = 1;
@@ -143,12 +149,12 @@ static heat3d_config group_config(const heat3d_server* s, int N) {
   c.batch = s->cfg.max_active;
   c.slices = 1;
   c.device = s->cfg.device;
-  c.stream = s->st;
+  c.stream = st;
   return c;
 }
 
 static size_t group_bytes(const heat3d_server* s, int N, size_t* ws_out) {
-  heat3d_config c = group_config(s, N);
+  heat3d_config c = group_config(s, N, nullptr);
   size_t ws = 0;
   if (heat3d_workspace_size(&c, &ws) != HEAT3D_OK) return 0;
   Grid g = make_grid(N);
@@ -157,6 +163,10 @@ static size_t group_bytes(const heat3d_server* s, int N, size_t* ws_out) {
   return ws + extra;
 }
 
+static void group_loop(heat3d_server* s, Group* g);
+
+// The group of size N, created (context, stream, pool chunk, thread) when
+// there is none; nullptr when the pool has no room for it.
 static Group* get_group(heat3d_server* s, int N) {
   auto it = s->groups.find(N);
   if (it != s->groups.end()) return it->second.get();
@@ -167,9 +177,14 @@ static Group* get_group(heat3d_server* s, int N) {
   auto g = std::make_unique<Group>();
   g->N = N;
   g->chunk = chunk;
-  heat3d_config c = group_config(s, N);
+  if (cudaStreamCreateWithFlags(&g->st, cudaStreamNonBlocking) != cudaSuccess) {
+    s->pool.release(chunk);
+    return nullptr;
+  }
+  heat3d_config c = group_config(s, N, g->st);
   if (heat3d_init(&c, &g->ctx) != HEAT3D_OK || heat3d_bind_workspace(g->ctx, chunk, ws) != HEAT3D_OK) {
     if (g->ctx) heat3d_destroy(g->ctx);
+    cudaStreamDestroy(g->st);
     s->pool.release(chunk);
     return nullptr;
   }
@@ -184,14 +199,25 @@ static Group* get_group(heat3d_server* s, int N) {
   g->slots.assign(s->cfg.max_active, nullptr);
   Group* raw = g.get();
   s->groups[N] = std::move(g);
+  raw->th = std::thread(group_loop, s, raw);
   return raw;
 }
 
+// Stops the group's thread (the group holds no request) and returns its memory.
 static void release_group(heat3d_server* s, int N) {
   auto it = s->groups.find(N);
   if (it == s->groups.end()) return;
-  heat3d_destroy(it->second->ctx);
-  s->pool.release(it->second->chunk);
+  Group* g = it->second.get();
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    g->stop = true;
+    g->cv.notify_all();
+  }
+  if (g->th.joinable()) g->th.join();
+  cudaStreamSynchronize(g->st);
+  heat3d_destroy(g->ctx);
+  cudaStreamDestroy(g->st);
+  s->pool.release(g->chunk);
   s->groups.erase(it);
 }
 
@@ -206,11 +232,14 @@ static int admit(heat3d_server* s, Group* g, int slot, Req& r) {
     for (int a = 0; a < 3; ++a)
       for (int i = 0; i < N; ++i) tab[((size_t)m * 3 + a) * N + i] = sin(M_PI * r.in.k[m][a] * (i + 1) * h);
   }
-  if (cudaMemcpyAsync(g->tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, s->st) != cudaSuccess ||
-      cudaMemcpyAsync(g->amp, amp.data(), sizeof(double) * kModes, cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+  // the next admission of this group reuses the tables: stream order keeps
+  // them intact until this request's kernel has read them, and a copy from
+  // pageable memory has taken the host data when the call returns
+  if (cudaMemcpyAsync(g->tab, tab.data(), sizeof(double) * tab.size(), cudaMemcpyHostToDevice, g->st) != cudaSuccess ||
+      cudaMemcpyAsync(g->amp, amp.data(), sizeof(double) * kModes, cudaMemcpyHostToDevice, g->st) != cudaSuccess)
     return HEAT3D_ECUDA;
   Grid gr = make_grid(N);
-  k_modes_ic<<<dim3((N + 31) / 32, (N + 7) / 8, N), dim3(32, 8), 0, s->st>>>(
+  k_modes_ic<<<dim3((N + 31) / 32, (N + 7) / 8, N), dim3(32, 8), 0, g->st>>>(
       gr, nm, g->tab, g->amp, g->ucur + (size_t)slot * gr.fs);
   count_launch();
   if (cudaGetLastError() != cudaSuccess) return HEAT3D_ECUDA;
@@ -242,7 +271,7 @@ static int step_group(heat3d_server* s, Group* g, std::vector<std::shared_ptr<Re
   if (rc < 0) return rc;
   for (int i = 0; i < A; ++i) {
     if (launch_copy(gr, M, g->ucur + (size_t)act[i]->slot * gr.fs, 0, L.U + (size_t)i * M * gr.fs, gr.fs,
-                    s->st) != cudaSuccess)
+                    g->st) != cudaSuccess)
       return HEAT3D_ECUDA;
   }
   rc = h3d_eval_F(c, 0, 0, A);
@@ -256,7 +285,7 @@ static int step_group(heat3d_server* s, Group* g, std::vector<std::shared_ptr<Re
   }
   for (int i = 0; i < A; ++i) {
     if (launch_copy(gr, 1, L.U + ((size_t)i * M + M - 1) * gr.fs, 0, g->ucur + (size_t)act[i]->slot * gr.fs, 0,
-                    s->st) != cudaSuccess)
+                    g->st) != cudaSuccess)
       return HEAT3D_ECUDA;
     Req& r = *act[i];
     r.step += 1;
@@ -278,74 +307,104 @@ static int step_group(heat3d_server* s, Group* g, std::vector<std::shared_ptr<Re
   return HEAT3D_OK;
 }
 
+// Marks finished requests done and frees their slots for waiting requests.
+static void complete(heat3d_server* s, Group* g, std::vector<std::shared_ptr<Req>>& fin) {
+  if (fin.empty()) return;
+  double t = now_s();
+  std::lock_guard<std::mutex> lk(s->mu);
+  for (auto& r : fin) {
+    r->t_done = t;
+    r->st.seconds = t - r->t_submit;
+    r->done = true;
+    if (r->status == HEAT3D_OK) s->latencies.push_back(r->st.seconds);
+  }
+  g->reserved -= (int)fin.size();
+  s->freed += 1;
+  s->cv_done.notify_all();
+  s->cv_submit.notify_all();
+}
+
+// A group's thread: starts the requests handed over to it, then advances its
+// residents by one time step per round on the group's stream.
+static void group_loop(heat3d_server* s, Group* g) {
+  cudaSetDevice(s->cfg.device);
+  for (;;) {
+    std::deque<std::shared_ptr<Req>> inc;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      g->cv.wait(lk, [&] { return s->stop || g->stop || !g->incoming.empty() || g->active() > 0; });
+      if (s->stop) return;
+      if (g->stop && g->incoming.empty() && g->active() == 0) return;
+      inc.swap(g->incoming);
+    }
+    std::vector<std::shared_ptr<Req>> fin;
+    for (auto& r : inc) {
+      int slot = -1;
+      for (int i = 0; i < (int)g->slots.size(); ++i)
+        if (!g->slots[i]) { slot = i; break; }
+      int rc = slot < 0 ? HEAT3D_EINVAL : admit(s, g, slot, *r);
+      if (rc < 0) {
+        r->status = rc;
+        fin.push_back(r);
+        continue;
+      }
+      g->slots[slot] = r;
+    }
+    int rc = step_group(s, g, fin);
+    if (rc < 0) {
+      for (auto& r : g->slots)
+        if (r) { r->status = rc; fin.push_back(r); r->slot = -1; }
+      std::fill(g->slots.begin(), g->slots.end(), nullptr);
+    }
+    complete(s, g, fin);
+  }
+}
+
+// The admission thread: hands requests, in arrival order, to their group when
+// it has a free slot (creating the group, or releasing idle groups of other
+// sizes to make room for it); a request that cannot be placed keeps its place.
 static void worker_loop(heat3d_server* s) {
   cudaSetDevice(s->cfg.device);
-  std::vector<std::shared_ptr<Req>> waiting;  // admitted order (FIFO)
+  std::vector<std::shared_ptr<Req>> waiting;  // arrival order (FIFO)
+  uint64_t seen = 0;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      bool idle = waiting.empty();
-      for (auto& kv : s->groups) idle = idle && kv.second->active() == 0;
-      if (idle && s->pending.empty()) {
-        s->cv_submit.wait(lk, [&] { return s->stop || !s->pending.empty(); });
-      }
+      s->cv_submit.wait(lk, [&] {
+        return s->stop || !s->pending.empty() || (!waiting.empty() && s->freed != seen);
+      });
       if (s->stop) return;
+      seen = s->freed;
       while (!s->pending.empty()) {
         waiting.push_back(s->pending.front());
         s->pending.pop_front();
       }
     }
-    // admission in arrival order; a request that cannot be placed keeps its place
     for (size_t q = 0; q < waiting.size();) {
       auto r = waiting[q];
       Group* g = get_group(s, r->in.N);
       if (!g) {
-        // free empty groups of other sizes to make room, then retry once
-        std::vector<int> empty;
-        for (auto& kv : s->groups)
-          if (kv.second->active() == 0 && kv.first != r->in.N) empty.push_back(kv.first);
-        for (int N : empty) release_group(s, N);
+        std::vector<int> idle;
+        {
+          std::lock_guard<std::mutex> lk(s->mu);
+          for (auto& kv : s->groups)
+            if (kv.second->reserved == 0 && kv.first != r->in.N) idle.push_back(kv.first);
+        }
+        for (int N : idle) release_group(s, N);
         g = get_group(s, r->in.N);
       }
-      int slot = -1;
-      if (g)
-        for (int i = 0; i < (int)g->slots.size(); ++i)
-          if (!g->slots[i]) { slot = i; break; }
-      if (!g || slot < 0) { ++q; continue; }
-      int rc = admit(s, g, slot, *r);
-      if (rc < 0) {
+      bool placed = false;
+      if (g) {
         std::lock_guard<std::mutex> lk(s->mu);
-        r->status = rc;
-        r->done = true;
-        r->t_done = now_s();
-        waiting.erase(waiting.begin() + q);
-        s->cv_done.notify_all();
-        continue;
+        if (g->reserved < s->cfg.max_active) {
+          g->incoming.push_back(r);
+          g->reserved += 1;
+          g->cv.notify_all();
+          placed = true;
+        }
       }
-      g->slots[slot] = r;
-      waiting.erase(waiting.begin() + q);
-    }
-    std::vector<std::shared_ptr<Req>> finished;
-    for (auto& kv : s->groups) {
-      std::vector<std::shared_ptr<Req>> fin;
-      int rc = step_group(s, kv.second.get(), fin);
-      if (rc < 0) {
-        for (auto& r : kv.second->slots)
-          if (r) { r->status = rc; fin.push_back(r); r->slot = -1; }
-        std::fill(kv.second->slots.begin(), kv.second->slots.end(), nullptr);
-      }
-      finished.insert(finished.end(), fin.begin(), fin.end());
-    }
-    if (!finished.empty()) {
-      double t = now_s();
-      std::lock_guard<std::mutex> lk(s->mu);
-      for (auto& r : finished) {
-        r->t_done = t;
-        r->st.seconds = t - r->t_submit;
-        r->done = true;
-        if (r->status == HEAT3D_OK) s->latencies.push_back(r->st.seconds);
-      }
-      s->cv_done.notify_all();
+      if (placed) waiting.erase(waiting.begin() + q);
+      else ++q;
     }
   }
 }
@@ -360,8 +419,7 @@ int heat3d_server_create(const heat3d_server_config* cfg, heat3d_server** out) {
     return HEAT3D_EINVAL;
   auto* s = new heat3d_server();
   s->cfg = *cfg;
-  if (cudaSetDevice(cfg->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaSetDevice(cfg->device) != cudaSuccess) {
     delete s;
     return HEAT3D_ECUDA;
   }
@@ -463,11 +521,13 @@ int heat3d_server_destroy(heat3d_server* s) {
     s->cv_submit.notify_all();
   }
   if (s->worker.joinable()) s->worker.join();
-  cudaStreamSynchronize(s->st);
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto& kv : s->groups) kv.second->cv.notify_all();
+  }
   std::vector<int> Ns;
   for (auto& kv : s->groups) Ns.push_back(kv.first);
   for (int N : Ns) release_group(s, N);
-  cudaStreamDestroy(s->st);
   delete s;
   return HEAT3D_OK;
 }

@@ -28,6 +28,7 @@
 // second neighbours, and returns the value whose max |.| is accumulated when
 // the launch asks for a norm.
 #pragma once
+#include <atomic>
 #include <type_traits>
 
 #include "kernels.cuh"
@@ -544,12 +545,12 @@ cudaError_t launch_tile(const Grid& g, int B, int nzc, int zc, const int* active
   using T = typename Op::T;
   constexpr int smem = tile_smem_bytes<T, ORDER, TYT, RY, D>();
   if (smem > 48 * 1024) {
-    static bool set = false;
-    if (!set) {
+    static std::atomic<bool> set{false};  // set once per process (one device)
+    if (!set.load()) {
       cudaError_t e = cudaFuncSetAttribute(k_tile<ORDER, TYT, RY, D, NORM, Op>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
-      set = true;
+      set.store(true);
     }
   }
   dim3 blk(32, TYT, 1);
@@ -815,12 +816,12 @@ cudaError_t launch_tile4(const Grid& g, int B, int nzc, int zc, const int* activ
                          cudaStream_t st) {
   constexpr int smem = tile4_smem<ORDER, TYT, RY, D>();
   if (smem > 48 * 1024) {
-    static bool set = false;
-    if (!set) {
+    static std::atomic<bool> set{false};  // set once per process (one device)
+    if (!set.load()) {
       cudaError_t e = cudaFuncSetAttribute(k_tile4<ORDER, TYT, RY, D, Op>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
       if (e != cudaSuccess) return e;
-      set = true;
+      set.store(true);
     }
   }
   dim3 blk(32, TYT, 1);

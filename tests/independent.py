@@ -225,3 +225,26 @@ def scalar_pfasst(lamF, lamG, MF, MG, dt, P, K, a0, nu, kappa, nsweeps_fine=1,
         if it >= 0:
             res = np.array([residual(aF[p], lamF, tF, QF, p * dt) for p in range(P)])
     return aF[:, MF - 1].copy(), aF, res
+
+
+def sdc_step_factor(z, M, nsweeps):
+    """R(z): the factor by which one step of M-node Gauss-Lobatto SDC (initial
+    value spread to every node, nsweeps implicit-Euler sweeps, exact solves,
+    no forcing) multiplies a mode of a' = lam a, with z = lam dt (Sec. 1.1,
+    the sweep equation in scalar form, step length 1)."""
+    tau = gl_nodes_legendre(M)
+    S = np.diff(qmatrix_numpy(tau), axis=0)
+    a = np.ones(M, dtype=np.complex128 if np.iscomplexobj(z) else np.float64)
+    for _ in range(nsweeps):
+        f = z * a
+        new = a.copy()
+        for m in range(M - 1):
+            dtm = tau[m + 1] - tau[m]
+            new[m + 1] = (new[m] - dtm * f[m + 1] + S[m] @ f) / (1.0 - dtm * z)
+        a = new
+    return a[-1]
+
+
+def lap7_eig(N, k):
+    """Eigenvalue of the 7-point Laplacian on sin(k1 pi x) sin(k2 pi y) sin(k3 pi z)."""
+    return float(sum(eig_1d(N, 2, ka) for ka in k))

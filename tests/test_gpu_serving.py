@@ -74,3 +74,53 @@ def test_admission_waits_for_memory_and_rejects_impossible(H):
         srv.submit(big)
     assert e.value.code == H.ENOMEM
     srv.close()
+
+
+def served_exact(r, nsweeps=4):
+    """The semi-discrete solution the served request must reach: every sine mode
+    of the initial value times R(nu lam_k dt)^n, R the scalar 3-node SDC step
+    factor with exact solves."""
+    from tests import independent as ind
+    n = int(round(r.T / r.dt))
+    u = np.zeros((r.N,) * 3)
+    for k1, k2, k3, a in r.modes:
+        z = r.nu * ind.lap7_eig(r.N, (k1, k2, k3)) * r.dt
+        u += a * ind.sdc_step_factor(z, 3, nsweeps) ** n * inputs.sine_mode(r.N, k1, k2, k3)
+    return u
+
+
+def test_serving_real_sizes_with_arrivals_in_flight(H):
+    """Grid sizes of the serving workload (63^3, 127^3, 255^3), mixed precision:
+    small requests submitted while large ones are resident are admitted at
+    once, run beside them (each grid size has its own stream) and finish
+    first; every result equals the semi-discrete solution of its request to
+    1e-9 of its initial value, and equals the same request served alone."""
+    import time
+    srv, pool = make_server(H, H.MIXED, pool_gb=24.0, max_active=4, sweeps=4)
+    big = inputs.request_stream(3, rate=0.0, seed=2024, sizes=(127,), horizons=(1.0,),
+                                dt=1.0 / 32)
+    big += inputs.request_stream(1, rate=0.0, seed=2025, sizes=(255,), horizons=(0.25,),
+                                 dt=1.0 / 32)
+    small = inputs.request_stream(3, rate=0.0, seed=2026, sizes=(63,), horizons=(0.25,),
+                                  dt=1.0 / 32)
+    t_sub, tickets = [], []
+    for r in big:
+        t_sub.append(time.perf_counter())
+        tickets.append(srv.submit(r))
+    time.sleep(0.05)
+    assert not all(srv.poll(t) for t in tickets), "the first requests finished too early"
+    for r in small:
+        t_sub.append(time.perf_counter())
+        tickets.append(srv.submit(r))
+    outs = [srv.wait(t) for t in tickets]
+    done = [ts + st["seconds"] for ts, (u, st) in zip(t_sub, outs)]
+    assert max(done[len(big):]) < max(done[:len(big)])
+    for r, (u, st) in zip(big + small, outs):
+        u0 = r.initial_value()
+        assert np.abs(u - served_exact(r)).max() <= 1e-9 * np.abs(u0).max(), (r.N, r.T)
+    srv.close()
+    for r, (u, _) in zip(small[:1] + big[3:], outs[len(big):len(big) + 1] + outs[3:4]):
+        solo, pool2 = make_server(H, H.MIXED, pool_gb=8.0, max_active=4, sweeps=4)
+        us, _ = solo.wait(solo.submit(r))
+        solo.close()
+        assert np.array_equal(us, u)

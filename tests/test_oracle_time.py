@@ -367,3 +367,19 @@ def test_pfasst_converges_at_the_paper_step_with_8_point_interpolation(oracle):
         res[interp] = (st["iters"], st["residual"])
     assert res[8][1] <= 1e-10 and res[8][0] <= 30
     assert res[2][1] > 1e-10
+
+
+@pytest.mark.parametrize("k,nu", [((2, 1, 3), 0.13), ((1, 1, 1), 0.05), ((8, 7, 8), 0.2)])
+def test_scalar_sdc_step_factor_is_the_oracle_on_one_mode(oracle, k, nu):
+    """The scalar step factor R(z) that the serving tests expect per mode equals
+    the oracle's 3-node, 4-sweep SDC on that mode with tight solves, and R
+    iterated to convergence is the collocation stability function."""
+    N, dt, n = 7, 1 / 32, 5
+    u0 = inputs.sine_mode(N, *k)
+    uT, rc, _ = oracle.sdc_run(N, 2, 3, oracle.Prob(nu=nu, forcing=0, mg_tol=1e-15, mg_max=200),
+                               dt, n, 4, u0)
+    z = nu * ind.lap7_eig(N, k) * dt
+    assert np.abs(uT - ind.sdc_step_factor(z, 3, 4) ** n * u0).max() <= 1e-14
+    Q = ind.qmatrix_numpy(ind.gl_nodes_legendre(3))
+    coll = np.linalg.solve(np.eye(3) - z * Q, np.ones(3))[-1]
+    assert abs(ind.sdc_step_factor(z, 3, 80) - coll) <= 1e-14
