@@ -17,11 +17,14 @@
 //    device address up with cudaGetSymbolAddress (host code cannot use the
 //    array's name as a device pointer) and builds the host-side solver state;
 //    make that first call before any stream capture.
+//  - Every call is synchronous: it waits for its stream to finish before it
+//    returns (host buffers are read and written on that stream).
 //  - All calls on a device share the array and it keeps the last call's
 //    contents; the solver clears what must start at zero (the residual norms
 //    each solve, the whole array when the grid, stencil or precision changes).
 //    Calls that overlap on the GPU (different streams or threads, in flight at
 //    the same time) race on the array and give wrong results: serialise them.
+//  - The failure message is kept per host thread.
 #include <stdio.h>
 
 #include <mutex>
@@ -45,7 +48,7 @@ struct DeviceState {
 
 std::mutex g_mu;
 DeviceState g_dev[kMaxDevices];
-char g_err[256] = "";
+thread_local char g_err[256] = "";
 
 int fail(int code, const char* msg) {
   snprintf(g_err, sizeof(g_err), "%s", msg);
@@ -91,9 +94,13 @@ int mg_vcycle_noalloc(int N, int order, int precision, double c, const double* r
     cfg.autotune = 0;    // tuning would create timing events
     cfg.use_graphs = 0;  // graphs would be instantiated (a resource allocation)
     size_t need = 0;
-    if (heat3d_workspace_size(&cfg, &need) != HEAT3D_OK || need > kNoAllocScratchBytes)
+    char msg[256] = "";
+    int rc0 = h3d_workspace_size_msg(&cfg, &need, msg, sizeof(msg));
+    if (rc0 != HEAT3D_OK) return fail(rc0, msg);
+    if (need > kNoAllocScratchBytes)
       return fail(HEAT3D_ENOMEM, "solver state does not fit in the no-allocation scratch array");
-    if (heat3d_init(&cfg, &s.ctx) != HEAT3D_OK) return fail(HEAT3D_EINVAL, "context set-up failed");
+    rc0 = heat3d_init(&cfg, &s.ctx);
+    if (rc0 != HEAT3D_OK) return fail(rc0, "context set-up failed");
     int rc = heat3d_bind_workspace(s.ctx, s.scratch, kNoAllocScratchBytes);  // zeroes the array
     if (rc != HEAT3D_OK) {
       heat3d_destroy(s.ctx);

@@ -52,6 +52,18 @@ int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...) {
     if (r_ < 0) return r_;                 \
   } while (0)
 
+// Two timing events destroyed on every exit path of the call that made them.
+struct EventPair {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  EventPair() = default;
+  EventPair(const EventPair&) = delete;
+  EventPair& operator=(const EventPair&) = delete;
+  ~EventPair() {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
 namespace h3d {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -1404,14 +1416,13 @@ int h3d_autotune(heat3d_ctx* c) {
   if (all_listed)
     for (int l = 0; l < c->cfg.nlevels; ++l) all_listed = tune_file_lookup(c, c->lv[l], tf) && all_listed;
   if (all_listed) return HEAT3D_OK;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
+  EventPair ev;
+  CK(cudaEventCreate(&ev.e0));
+  CK(cudaEventCreate(&ev.e1));
   const long long l0 = h3d::launches_total();
-  int rc = h3d_tsize(c) == 4 ? autotune_T<float>(c, e0, e1) : autotune_T<double>(c, e0, e1);
+  int rc = h3d_tsize(c) == 4 ? autotune_T<float>(c, ev.e0, ev.e1)
+                             : autotune_T<double>(c, ev.e0, ev.e1);
   h3d::launches_adjust(-(h3d::launches_total() - l0));  // tuning launches are not work
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   CK(cudaStreamSynchronize(c->st));
   if (rc == HEAT3D_OK && tf && tf[0])
     for (int l = 0; l < c->cfg.nlevels; ++l) tune_file_append(c, c->lv[l], tf);
@@ -1462,6 +1473,22 @@ int h3d_store_dense(heat3d_ctx* c, int lev, const double* src_pitched, double* d
     if (!(c)) return HEAT3D_EINVAL;                                                    \
     if (!(c)->bound) return h3d_fail((c), HEAT3D_ESTATE, "no workspace bound");        \
   } while (0)
+
+int h3d_workspace_size_msg(const heat3d_config* cfg, size_t* bytes, char* msg, size_t msg_len) {
+  if (!cfg || !bytes) return HEAT3D_EINVAL;
+  heat3d_ctx tmp;
+  int rc = validate(&tmp, cfg);
+  if (rc >= 0) {
+    tmp.cfg = *cfg;
+    rc = setup_levels(&tmp);
+  }
+  if (rc < 0) {
+    if (msg && msg_len) snprintf(msg, msg_len, "%s", tmp.err);
+    return rc;
+  }
+  *bytes = plan(&tmp, nullptr);
+  return HEAT3D_OK;
+}
 
 extern "C" {
 
@@ -1642,10 +1669,10 @@ int mg_vcycle(heat3d_ctx* c, int level, double cc, const double* rhs, double* u,
   if (level < 0 || level >= c->cfg.nlevels || !rhs || !u || max_cycles < 0 || !(cc >= 0))
     return h3d_fail(c, HEAT3D_EINVAL, "bad arguments");
   SdcLevel& L = c->lv[level];
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, c->st));
+  EventPair ev;
+  CK(cudaEventCreate(&ev.e0));
+  CK(cudaEventCreate(&ev.e1));
+  CK(cudaEventRecord(ev.e0, c->st));
   double* ub = L.abi_p0;  // pitched solution
   double* bb = L.abi_p1;  // pitched right-hand side
   RET(h3d_load_dense(c, level, rhs, bb));
@@ -1658,12 +1685,10 @@ int mg_vcycle(heat3d_ctx* c, int level, double cc, const double* rhs, double* u,
                           : HEAT3D_OK;
   if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
   RET(h3d_store_dense(c, level, ub, u));
-  CK(cudaEventRecord(e1, c->st));
-  CK(cudaEventSynchronize(e1));
+  CK(cudaEventRecord(ev.e1, c->st));
+  CK(cudaEventSynchronize(ev.e1));
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   loc.seconds = ms * 1e-3;
   loc.bytes = c->bytes;
   if (stats) *stats = loc;
@@ -1752,26 +1777,20 @@ int pfasst_run(heat3d_ctx* c, const double* u0, double* uT, heat3d_stats* stats)
   NEED_BOUND(c);
   if (!u0 || !uT) return h3d_fail(c, HEAT3D_EINVAL, "null u0/uT");
   SdcLevel& F = c->lv[0];
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  CK(cudaEventRecord(e0, c->st));
+  EventPair ev;
+  CK(cudaEventCreate(&ev.e0));
+  CK(cudaEventCreate(&ev.e1));
+  CK(cudaEventRecord(ev.e0, c->st));
   heat3d_stats loc{};
   c->bytes = 0;
   RET(h3d_load_dense(c, 0, u0, F.abi_u));
   int rc = h3d_run(c, F.abi_u, &loc);
-  if (rc < 0 && rc != HEAT3D_ENOTCONV) {
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    return rc;
-  }
+  if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
   RET(h3d_store_dense(c, 0, F.abi_u, uT));
-  CK(cudaEventRecord(e1, c->st));
-  CK(cudaEventSynchronize(e1));
+  CK(cudaEventRecord(ev.e1, c->st));
+  CK(cudaEventSynchronize(ev.e1));
   float ms = 0;
-  cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  cudaEventElapsedTime(&ms, ev.e0, ev.e1);
   loc.seconds = ms * 1e-3;
   loc.bytes = c->bytes;
   if (stats) *stats = loc;

@@ -119,6 +119,8 @@ int h3d_prof_begin(heat3d_ctx* c, int cls);
 void h3d_prof_end(heat3d_ctx* c, int pair, double bytes, double dpops, double flops);
 
 int h3d_fail(heat3d_ctx* c, int code, const char* fmt, ...);
+// heat3d_workspace_size that also copies a validation failure's message to msg.
+int h3d_workspace_size_msg(const heat3d_config* cfg, size_t* bytes, char* msg, size_t msg_len);
 size_t h3d_tsize(const heat3d_ctx* c);
 void h3d_fill_item(heat3d_ctx* c, int lev, int item, double t0);
 int h3d_upload_items(heat3d_ctx* c, int lev, int b0, int B);

@@ -61,3 +61,27 @@ def test_noalloc_tolerance_mode_and_limits(H):
     with pytest.raises(H.Heat3DError) as e:
         H.mg_vcycle_noalloc(127, order, H.FP64, c, np.zeros((127,) * 3), np.zeros((127,) * 3), 1, -1.0)
     assert e.value.code == H.EINVAL and "63" in str(e.value)
+
+
+def test_noalloc_mixed_precision_and_switching(H):
+    """Mixed precision (FP32 V-cycles inside FP64 refinement) at N = 63 with the
+    wide stencil, against mg_vcycle on a mixed context; then FP64, mixed and
+    FP64 again at one N, each call against its own reference (a change of
+    precision rebuilds the solver state inside the shared array)."""
+    N, order, c = 63, 4, 0.002
+    b = inputs.random_field(N, seed=31)
+    u0 = inputs.random_field(N, seed=32, scale=0.1)
+    refs = {}
+    for prec in (H.FP64, H.MIXED):
+        ctx = H.Context(H.make_config((N, order, 3), precision=prec))
+        r = torch.from_numpy(u0.copy()).cuda()
+        H.mg_vcycle(ctx, 0, c, torch.from_numpy(b).cuda(), r, 3, -1.0)
+        refs[prec] = r.cpu().numpy()
+        ctx.close()
+    for prec in (H.MIXED, H.FP64, H.MIXED, H.FP64):
+        got = torch.from_numpy(u0.copy()).cuda()
+        rc, st = H.mg_vcycle_noalloc(N, order, prec, c, torch.from_numpy(b).cuda(), got, 3, -1.0)
+        assert rc == H.OK and st["vcycles"] == 3
+        g = got.cpu().numpy()
+        tol = 1e-11 if prec == H.FP64 else 1e-9
+        assert np.abs(g - refs[prec]).max() <= tol * np.abs(refs[prec]).max(), prec
