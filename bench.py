@@ -37,8 +37,8 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # DRAM bytes (read + write) per launch of the roofline kernel, from one ncu
-# capture of the kernel as it is now (profiles/stencils_fine_255_*.md); key:
-# (precision, fine stencil order, N).  Must be cleared when that kernel changes.
+# capture of the kernel as it is now; key: (precision, fine stencil order, N).
+# Must be cleared when that kernel changes.
 TRAFFIC_BYTES = {
     ("fp64", 4, 255): 378.9e6,   # k_tile OpJacobi<double, 4>, fine level
     ("fp64", 19, 255): 376.4e6,  # k_tile OpJacobi<double, 19>, fine level
@@ -166,11 +166,18 @@ class ClockSampler:
                 "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons, "samples": len(rows)}
 
 
+def mixed_inner():
+    return int(os.environ.get("HEAT3D_INNER", "3"))
+
+
 def make_cfg(H, w, precision=None, slices=None, graphs=True, mg_rel=None, interp=None):
     prec = H.MIXED if (precision or w["precision"]) == "mixed" else H.FP64
     # mg_rel > 0: each solve stops at max(mg_tol, mg_rel x the sweep's incoming residual)
     mg_rel = w.get("mg_rel", 0.0) if mg_rel is None else mg_rel
-    inner = 2 if prec == H.MIXED else 1  # FP32 V-cycles per FP64 residual
+    # FP32 V-cycles per FP64 residual in mixed precision: 3 was fastest of
+    # {2, 3, 4, 6} on the 255^3 MLSDC workload at equal error (HEAT3D_INNER
+    # overrides it)
+    inner = mixed_inner() if prec == H.MIXED else 1
     return H.make_config(w["fine"], w["coarse"], dt=w["dt"], T=w["dt"],
                          sweeps_fine=w["sweeps_fine"], sweeps_coarse=w["sweeps_coarse"],
                          slices=slices or w["slices"], iters=w["iters"], tol_sdc=w["tol_sdc"],
@@ -305,12 +312,18 @@ def run_ours(args, w, rank, world):
         per_launch_s = prof["ms"] / 1e3 / prof["launches"]
         dp_per_launch = prof["dp_ops"] / prof["launches"]
         fp64_peak = 152 * 2 * sm_max * 1e6 / 1e9  # Gop/s: 2 FP64 pipe ops / clk / SM
+        try:
+            fp64_probe = H.heat3d_fp64_probe(ctx.stream) / 1e9
+        except Exception:  # noqa: BLE001 - context only
+            fp64_probe = None
         if w["precision"] == "fp64" or prof_class == H.PROF_RESID64_FINE:
             achieved = dp_per_launch / per_launch_s / 1e9
             roof = {"bound": "alu", "kernel": "jacobi_fine_fp64" if prof_class == 1 else "resid64_fine",
                     "achieved": round(achieved, 2), "peak": round(fp64_peak, 1),
                     "unit": "Gop/s (FP64 pipe)", "frac": round(achieved / fp64_peak, 4),
                     "peak_source": f"152 SMs x 2 FP64 ops/clk x {sm_max:.0f} MHz",
+                    "fp64_fma_probe": None if fp64_probe is None else round(fp64_probe, 1),
+                    "frac_of_probe": None if not fp64_probe else round(achieved / fp64_probe, 4),
                     "hbm_achieved_gbs": round(prof["bytes"] / prof["launches"] / per_launch_s / 1e9, 1),
                     "hbm_frac_of_measured": round(prof["bytes"] / prof["launches"] / per_launch_s / 1e9
                                                   / pk["hbm_gbs"], 4),
@@ -367,6 +380,8 @@ def run_variant(args, w, u0, uT, out, precision, mg_rel, interp=None, tol_sdc=No
         H.heat3d_set_interval(cm, 0.0, args.warmup * w["dt"])
         H.pfasst_run(cm, u0_d, o, allow_notconv=True)
     H.heat3d_set_interval(cm, 0.0, args.steps * w["dt"])
+    if precision == "mixed":  # times the fine FP32 Jacobi launches (HBM bound)
+        H.heat3d_profile(cm, H.PROF_JACOBI_FINE)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(cm.stream)
@@ -374,13 +389,28 @@ def run_variant(args, w, u0, uT, out, precision, mg_rel, interp=None, tol_sdc=No
     e1.record(cm.stream)
     torch.cuda.synchronize()
     s_m = e0.elapsed_time(e1) / 1e3
+    roof32 = None
+    if precision == "mixed":
+        prof = H.heat3d_profile_read(cm)
+        H.heat3d_profile(cm, H.PROF_OFF)
+        if prof["launches"] > 0 and prof["ms"] > 0:
+            pk, pk_src = peaks()
+            per = prof["ms"] / 1e3 / prof["launches"]
+            gbs = prof["bytes"] / prof["launches"] / per / 1e9
+            roof32 = {"bound": "hbm", "kernel": "jacobi_fine_fp32", "achieved": round(gbs, 1),
+                      "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / pk["hbm_gbs"], 4),
+                      "launches": prof["launches"], "avg_launch_us": round(per * 1e6, 2),
+                      "algorithmic_bytes_per_launch": round(prof["bytes"] / prof["launches"]),
+                      "traffic": TRAFFIC_BYTES.get(("fp32-jacobi", w["fine"][1], w["fine"][0])),
+                      "peak_file": pk_src}
     um = o.cpu().numpy()
     Nf = w["fine"][0]
     a_pde = analytic_amplitude(args.steps * w["dt"])
     err_m = float(np.abs(um - a_pde * inputs.sine_mode(Nf)).max() / abs(a_pde))
     cm.close()
     return {"precision": precision, "mg_rel": mg_rel, "interp": interp or w.get("interp", 2),
-            "tol_sdc": wv["tol_sdc"],
+            "tol_sdc": wv["tol_sdc"], "inner": mixed_inner() if precision == "mixed" else 1,
+            "roofline_fp32": roof32,
             "value": Nf ** 3 * args.steps / s_m, "ms_per_step": s_m * 1e3 / args.steps,
             "rel_err_vs_pde_solution": err_m,
             "max_rel_diff_vs_fp64": float(np.abs(um - uT).max() / np.abs(uT).max()),

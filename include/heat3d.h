@@ -249,6 +249,15 @@ int heat3d_profile_read(heat3d_ctx* ctx, double* ms, long long* launches, double
  * Synchronises the stream; other values: HEAT3D_EINVAL. */
 int heat3d_selftest_barrier(void* stream, int absent_block);
 
+/* FP64 FMA throughput of the current device (fused multiply-adds per second,
+ * one FP64-pipe operation each): independent FMA chains on 4 blocks of 512
+ * threads per SM, best of three timed launches on `stream` (a cudaStream_t;
+ * NULL: legacy).  No counterpart in the paper: it measures the denominator of
+ * the FP64 stencil kernels' roofline (they are bound by the FP64 pipe, not by
+ * memory).  Synchronises the stream; allocates no device memory.
+ * HEAT3D_EINVAL for a NULL output, HEAT3D_ECUDA on a CUDA error. */
+int heat3d_fp64_probe(void* stream, double* fma_per_s);
+
 /* ---------------------------------------------------------------------- */
 /* Solve without any device allocation (no counterpart in the paper).       */
 /* ---------------------------------------------------------------------- */
@@ -262,15 +271,19 @@ int heat3d_selftest_barrier(void* stream, int absent_block);
  *  - N = 2^k - 1 <= 63; larger N returns HEAT3D_EINVAL.  order 2 or 4;
  *    precision HEAT3D_FP64 or HEAT3D_MIXED; c, max_cycles, tol as mg_vcycle.
  *  - rhs, u: host or device, dense N^3 FP64; u is the warm start and result.
- *  - Runs on the current device and `stream`, and returns with u complete.
+ *  - Runs on the current device and `stream`.  Every call is synchronous:
+ *    it waits for `stream` to finish before it returns, with u complete
+ *    (host buffers are read and written on that stream).
  *  - The first call on a device looks up the array's device address and sets
  *    up the solver state: make it before any stream capture.
  *  - Calls share the array (it keeps the last call's contents; the solver
  *    clears what must start at zero).  Calls that overlap on the GPU race:
- *    serialise them.  stats->seconds is not measured (0). */
+ *    serialise them.  stats->seconds is not measured (0).
+ *  - Errors: HEAT3D_EINVAL (arguments, N), HEAT3D_ENOMEM (the solver state
+ *    does not fit in the array), HEAT3D_ECUDA, or the solve's own code. */
 int mg_vcycle_noalloc(int N, int order, int precision, double c, const double* rhs, double* u,
                       int max_cycles, double tol, void* stream, heat3d_stats* stats);
-/* Message of the last mg_vcycle_noalloc failure. */
+/* Message of the calling thread's last mg_vcycle_noalloc failure. */
 const char* mg_vcycle_noalloc_last_error(void);
 
 /* ---------------------------------------------------------------------- */

@@ -50,6 +50,9 @@ cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, lon
 
 // Damped Jacobi: out = e + wd (r - A e).  With u64 != nullptr the result is
 // added to u64 (u64 += out) instead of being stored in out.
+// Reads and clears the FP32 tile's lost-copy flag (synchronises the stream).
+cudaError_t loader_timeouts_take(cudaStream_t st, int* flag);
+
 template <typename T>
 cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
                           double* u64, long long u64_stride, const Coef<T>* coef,

@@ -1297,15 +1297,23 @@ static bool tune_log() {
   return v && v[0] == '1';
 }
 
-// vec4: the operator has the four-points-per-thread FP32 tile (kinds 7-10).
+// vec4: the operator has the four-points-per-thread FP32 tiles (kinds 7-14,
+// and 15-22 with the z neighbours in registers, 19-22 loading planes by
+// TMA); the latter also try a chunk of 12 planes and the chunks that fill
+// one or two whole waves of the GPU.
 static std::vector<Shape> shape_candidates(int N, bool vec4) {
   std::vector<Shape> v;
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
     if (zc <= N) v.push_back(Shape{1, zc});
-  if (N >= 16)
+  if (N >= 16) {
     for (int kind = 2; kind <= (vec4 ? 14 : 6); ++kind)
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
+    if (vec4)  // zc -1, -2: the chunk length that fills one or two whole waves
+      for (int kind = 15; kind <= 22; ++kind)
+        for (int zc : {8, 12, 16, 32, -1, -2})
+          if (zc <= N) v.push_back(Shape{kind, zc});
+  }
   return v;
 }
 
@@ -1468,6 +1476,16 @@ int h3d_store_dense(heat3d_ctx* c, int lev, const double* src_pitched, double* d
   return HEAT3D_OK;
 }
 
+// A lost TMA plane copy in an FP32 stencil (bounded wait gave up): the
+// affected tile was not computed, so the call fails with HEAT3D_ETIMEOUT.
+static int check_loader(heat3d_ctx* c) {
+  if (h3d_tsize(c) != 4) return HEAT3D_OK;
+  int flag = 0;
+  CK(loader_timeouts_take(c->st, &flag));
+  if (flag) return h3d_fail(c, HEAT3D_ETIMEOUT, "an FP32 stencil's TMA plane copy did not complete");
+  return HEAT3D_OK;
+}
+
 #define NEED_BOUND(c)                                                                  \
   do {                                                                                 \
     if (!(c)) return HEAT3D_EINVAL;                                                    \
@@ -1591,7 +1609,7 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   // every shape must give bitwise the same results)
   if (const char* f = getenv("HEAT3D_SHAPE")) {
     int kind = 0, zc = 0;
-    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 14 && zc >= 1) {
+    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 22 && zc >= -2 && zc != 0) {
       for (int l = 0; l < c->cfg.nlevels; ++l) {
         SdcLevel& L = c->lv[l];
         for (int k = 0; k < L.nmg; ++k)
@@ -1684,6 +1702,7 @@ int mg_vcycle(heat3d_ctx* c, int level, double cc, const double* rhs, double* u,
   int rc = max_cycles > 0 ? h3d_mg_solve(c, level, slot, 0, 1, ub, 0, bb, 0, max_cycles, tol, &loc)
                           : HEAT3D_OK;
   if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
+  RET(check_loader(c));
   RET(h3d_store_dense(c, level, ub, u));
   CK(cudaEventRecord(ev.e1, c->st));
   CK(cudaEventSynchronize(ev.e1));
@@ -1742,6 +1761,7 @@ int sdc_sweep(heat3d_ctx* c, int level, int batch_begin, int batch_count, heat3d
   c->bytes = 0;
   int rc = h3d_sweep(c, level, batch_begin, batch_count, -1.0, &loc);
   CK(cudaStreamSynchronize(c->st));
+  RET(check_loader(c));
   loc.bytes = c->bytes;
   if (stats) *stats = loc;
   return rc;
@@ -1786,6 +1806,7 @@ int pfasst_run(heat3d_ctx* c, const double* u0, double* uT, heat3d_stats* stats)
   RET(h3d_load_dense(c, 0, u0, F.abi_u));
   int rc = h3d_run(c, F.abi_u, &loc);
   if (rc < 0 && rc != HEAT3D_ENOTCONV) return rc;
+  RET(check_loader(c));
   RET(h3d_store_dense(c, 0, F.abi_u, uT));
   CK(cudaEventRecord(ev.e1, c->st));
   CK(cudaEventSynchronize(ev.e1));

@@ -283,6 +283,11 @@ static int step_group(heat3d_server* s, Group* g, std::vector<std::shared_ptr<Re
     if (rc == HEAT3D_ENOTCONV) status = rc;
     else if (rc < 0) return rc;
   }
+  if (s->cfg.precision == HEAT3D_MIXED) {  // a lost TMA plane copy fails the step
+    int lost = 0;
+    if (loader_timeouts_take(g->st, &lost) != cudaSuccess) return HEAT3D_ECUDA;
+    if (lost) return HEAT3D_ETIMEOUT;
+  }
   for (int i = 0; i < A; ++i) {
     if (launch_copy(gr, 1, L.U + ((size_t)i * M + M - 1) * gr.fs, 0, g->ucur + (size_t)act[i]->slot * gr.fs, 0,
                     g->st) != cudaSuccess)

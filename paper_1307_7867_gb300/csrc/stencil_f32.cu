@@ -17,4 +17,18 @@ namespace h3d {
 H3D_INST(float)
 #undef H3D_INST
 
+// Reads and clears the flag the FP32 tile sets when a TMA plane copy never
+// completed (the kernel then returns without finishing its tile).
+cudaError_t loader_timeouts_take(cudaStream_t st, int* flag) {
+  *flag = 0;
+  cudaError_t e = cudaMemcpyFromSymbolAsync(flag, g_zq_timeout, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess && *flag) {
+    const int zero = 0;
+    e = cudaMemcpyToSymbolAsync(g_zq_timeout, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e;
+}
+
 }  // namespace h3d

@@ -28,6 +28,11 @@
 // second neighbours, and returns the value whose max |.| is accumulated when
 // the launch asks for a norm.
 #pragma once
+#include <cuda.h>  // CUtensorMap (the tensor map of the TMA loader)
+#include <cudaTypedefs.h>
+#include <string.h>
+
+#include <algorithm>
 #include <atomic>
 #include <type_traits>
 
@@ -100,6 +105,55 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int n>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(n) : "memory");
+}
+
+// mbarrier and TMA (tensor memory access) primitives of the FP32 plane loader.
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for phase `parity` of the barrier to complete; gives up (false) after
+// about one second of SM clock cycles, so that a lost copy cannot hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+// Orders this thread's earlier shared-memory accesses before later copies of
+// the async proxy (TMA) into the same memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+// One box of a 4-D tensor map (x, y, z, item) into shared memory, completing
+// `bytes` on the barrier.  x must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y, int z,
+                                            int b, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(b), "r"(bar)
+      : "memory");
 }
 
 template <typename T, int ORDER>
@@ -222,6 +276,8 @@ struct OpJacobi {
   double* u_;
   T e2c;
   __device__ const T* src(int b) const { return e + b * fs; }
+  __host__ __device__ const T* src_base() const { return e; }
+  __host__ __device__ long long src_stride() const { return fs; }
   __device__ void init(int b) {
     d = coef[b].d;
     ec = coef[b].e;
@@ -302,6 +358,8 @@ struct OpResid {
   T* o_;
   T e2c;
   __device__ const T* src(int b) const { return e + b * fs; }
+  __host__ __device__ const T* src_base() const { return e; }
+  __host__ __device__ long long src_stride() const { return fs; }
   __device__ void init(int b) {
     d = coef[b].d;
     ec = coef[b].e;
@@ -830,6 +888,375 @@ cudaError_t launch_tile4(const Grid& g, int B, int nzc, int zc, const int* activ
   return cudaSuccess;
 }
 
+// FP32 tile with the z neighbours in registers (7-point and wide stencils):
+// as k_tile4 (a warp covers 128 consecutive x points of one row, four per
+// thread, float4 accesses), but each thread keeps its own four points of the
+// planes k-R .. k+R in a register queue, so that the ring in shared memory
+// only has to hold the plane being computed (for the x and y neighbours), the
+// planes up to k+R (whose own points enter the queue) and the D planes in
+// flight: R + D + 1 planes instead of 2R + D + 1, and four fewer 16-byte
+// shared reads per row.  The ring size is a multiple of the queue length
+// 2R + 1 and the z loop is unrolled by it, so ring slots and queue entries
+// are compile-time registers.  Boundary cells in x and y are written into
+// the ring as in k_tile4, those in z replaced in registers.  Planes arrive
+// either by
+// 16-byte cp.async copies of every thread (TMA = 0) or as one TMA box per
+// plane issued by one thread, completing on an mbarrier per ring slot
+// (TMA = 1; waits bounded, a lost copy sets g_zq_timeout and the block
+// returns).  The per-point sums are formed as in k_tile4, so the results are
+// bitwise identical.
+__device__ int g_zq_timeout;
+
+template <int ORDER, int DEEP>
+__host__ __device__ constexpr int zq_depth() {  // prefetch depth: R + D + 1 must be a multiple of 2R + 1
+  return ORDER == 4 ? (DEEP ? 7 : 2) : (DEEP ? 7 : 4);
+}
+template <int ORDER, int TYT>
+__host__ __device__ constexpr int zq_slot_floats() {  // one plane of the ring, 128-byte aligned
+  return ((TYT + 2 * (ORDER == 4 ? 2 : 1)) * (128 + 8) + 31) / 32 * 32;
+}
+template <int ORDER, int TYT, int DEEP>
+__host__ __device__ constexpr int zq_smem() {
+  return ((ORDER == 4 ? 2 : 1) + zq_depth<ORDER, DEEP>() + 1) * zq_slot_floats<ORDER, TYT>() * 4 + 128;
+}
+template <int ORDER, int TYT, int DEEP, int REGS>
+constexpr int zq_min_blocks() {
+  return (232448 / zq_smem<ORDER, TYT, DEEP>()) < (65536 / (32 * TYT * REGS))
+             ? (232448 / zq_smem<ORDER, TYT, DEEP>())
+             : (65536 / (32 * TYT * REGS));
+}
+// registers the queue kernel keeps without spilling: the wide stencil's
+// queue and y neighbours take 16 more than k_tile4's floor
+template <int ORDER, int TMA, typename Op>
+constexpr int zq_reg_floor() {
+  return ORDER != 4 ? Op::kRegFloor : Op::kRegFloor >= 80 ? Op::kRegFloor : 80;
+}
+
+template <int ORDER, int TYT, int DEEP, int TMA, typename Op>
+__global__ void __launch_bounds__(32 * TYT, (zq_min_blocks<ORDER, TYT, DEEP, zq_reg_floor<ORDER, TMA, Op>()>()))
+    k_zq4(Grid g, int nzc, int zc, const int* active, Op op, const __grid_constant__ CUtensorMap tmap) {
+  using T = typename Op::T;
+  static_assert(sizeof(T) == 4, "k_zq4 is the FP32 path");
+  static_assert(ORDER == 2 || ORDER == 4, "k_zq4: 7-point and wide stencils");
+  constexpr int R = ORDER == 4 ? 2 : 1;
+  constexpr int D = zq_depth<ORDER, DEEP>();
+  constexpr int NB = R + D + 1;  // ring slots
+  constexpr int QL = 2 * R + 1;  // queue length
+  static_assert(NB % QL == 0, "ring size must be a multiple of the queue length");
+  constexpr int TX = 128, TY = TYT;
+  constexpr int XH = 4;
+  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R;
+  constexpr int CH = SX / XH;
+  constexpr int NT = 32 * TYT;
+  constexpr int PS = zq_slot_floats<ORDER, TYT>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bars[NB];
+  float* ring = reinterpret_cast<float*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int b = blockIdx.z / nzc;
+  if (active && !active[b]) return;  // uniform over the block
+  const int N = g.N;
+  const int plane = (int)g.plane;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = (blockIdx.z - b * nzc) * zc, z1 = min(N, z0 + zc);
+  Op o = op;
+  o.init(b);
+  const float* __restrict__ u = o.src(b);
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  const unsigned bar_s = (unsigned)__cvta_generic_to_shared(bars);
+
+  constexpr int NCH = TMA ? 1 : (SY * CH + NT - 1) / NT;
+  int soff[NCH], goff[NCH];
+  if (!TMA) {
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      const int c = tid + q * NT;
+      const int ry = c / CH, cx = c - ry * CH;
+      const int cgy = y0 - R + ry, cgx = x0 - XH + cx * XH;
+      const bool ok = c < SY * CH && cgy >= 0 && cgy < N && cgx >= 0 && cgx + XH <= g.px;
+      soff[q] = ok ? ry * SX + cx * XH : -1;
+      goff[q] = cgy * g.px + cgx;
+    }
+  } else if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) mbar_init(bar_s + 8u * q, 1);
+    mbar_init_fence();
+  }
+  if (TMA) __syncthreads();
+  // plane p lives in slot (p - z0 + R) mod NB.  cp.async: one commit group per
+  // plane, empty for planes outside the domain or past the chunk, so that group
+  // counts match.  TMA: thread 0 arms the slot's barrier with the box's bytes
+  // and issues the box, or only arrives for a plane that is not copied, so that
+  // every slot completes one barrier phase per plane it is assigned.
+  auto issue = [&](int z, int slot) {
+    const bool copy = z >= 0 && z < N && z <= z1 - 1 + R;
+    if (TMA) {
+      if (tid == 0) {
+        const unsigned bar = bar_s + 8u * slot;
+        if (copy) {
+          fence_proxy_async_smem();
+          mbar_expect_tx(bar, (unsigned)(SY * SX * 4));
+          tma_load_4d(ring_s + (unsigned)(slot * PS) * 4u, &tmap, x0 - XH, y0 - R, z, b, bar);
+        } else {
+          mbar_arrive(bar);
+        }
+      }
+    } else {
+      if (copy) {
+        const unsigned dst = ring_s + (unsigned)(slot * PS) * 4u;
+        const float* uz = u + z * plane;
+#pragma unroll
+        for (int q = 0; q < NCH; ++q)
+          if (soff[q] >= 0) cp_async16(dst + (unsigned)soff[q] * 4u, uz + goff[q]);
+      }
+      cp_async_commit();
+    }
+  };
+  // TMA: waits for plane p (fill number (p - z0 + R) / NB of its slot); false
+  // if the copy never completed
+  auto arrived = [&](int p, int slot) -> bool {
+    if (!TMA) return true;
+    const unsigned parity = (unsigned)((p - z0 + R) / NB) & 1u;
+    return mbar_wait_bounded(bar_s + 8u * slot, parity);
+  };
+  // after a lost copy: thread 0 waits (bounded) for every slot's last
+  // fill, records the fault, and the whole block returns
+  auto give_up = [&](int last_issued) {
+    if (tid == 0) {
+      atomicExch(&g_zq_timeout, 1);
+      for (int p = last_issued; p > last_issued - NB && p >= z0 - R; --p)
+        mbar_wait_bounded(bar_s + 8u * ((p - z0 + R) % NB), (unsigned)((p - z0 + R) / NB) & 1u);
+    }
+  };
+
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = x0 + 4 * tx;
+  const int j = y0 + ty;
+  const int sbase = (R + ty) * SX + XH + 4 * tx;
+  const int nx = N - i;  // points of the thread's four inside the grid
+  auto own = [&](int slot) { return *reinterpret_cast<const float4*>(ring + slot * PS + sbase); };
+  // boundary cells of a plane in the ring, as in k_tile4: x and y indices -1
+  // and N read 0, the wide stencil's ghosts -2 and N+1 minus the cell at 0
+  // and N-1 (corners are never read by these stencils).  With the TMA loader
+  // the writing threads then order their writes before the slot's next copy.
+  const int cxN = XH + N - x0;
+  const bool xlo = x0 == 0, xhi = cxN < SX;
+  const int ryN = N - (y0 - R);
+  const bool ylo = y0 < R, yhi = ryN < SY;
+  const bool edge = xlo || xhi || ylo || yhi;  // the same for the whole block
+  auto fill = [&](int z, int slot) {
+    if (z < 0 || z >= N || !edge) return;
+    float* P = ring + slot * PS;
+    if (xlo || xhi)
+      for (int r = tid; r < SY; r += NT) {
+        const int y = y0 - R + r;
+        if (y < 0 || y >= N) continue;
+        float* row = P + r * SX;
+        if (xlo) {
+          if (R == 2) row[XH - 2] = -row[XH];
+          row[XH - 1] = 0.f;
+        }
+        if (xhi) {
+          if (R == 2 && cxN + 1 < SX) row[cxN + 1] = -row[cxN - 1];
+          row[cxN] = 0.f;
+        }
+      }
+    if (ylo || yhi)
+      for (int c = tid; c < SX; c += NT) {
+        if (ylo) {
+          if (R == 2) P[c] = -P[R * SX + c];
+          P[(R - 1) * SX + c] = 0.f;
+        }
+        if (yhi) {
+          if (R == 2 && ryN + 1 < SY) P[(ryN + 1) * SX + c] = -P[(ryN - 1) * SX + c];
+          P[ryN * SX + c] = 0.f;
+        }
+      }
+    if (TMA) fence_proxy_async_smem();
+  };
+
+  // prologue: the first NB planes (z0-R .. z0+D); the queue takes the own
+  // points of z0-R .. z0+R-1; planes z0 .. z0+R get their boundary cells
+#pragma unroll 1
+  for (int q = 0; q < NB; ++q) issue(z0 - R + q, q);
+  if (TMA) {
+    bool ok = true;
+#pragma unroll
+    for (int q = 0; q <= 2 * R; ++q) ok = arrived(z0 - R + q, q) && ok;
+    if (__syncthreads_or(!ok)) {
+      give_up(z0 + D);
+      return;
+    }
+  } else {
+    cp_async_wait<D - R>();  // planes up to z0+R have arrived
+    __syncthreads();
+  }
+  float4 qv[QL];
+#pragma unroll
+  for (int q = 0; q < 2 * R; ++q) qv[q] = own(q);
+#pragma unroll
+  for (int q = 0; q <= R; ++q) fill(z0 + q, R + q);
+  __syncthreads();
+  // slots 0 .. R-2 (planes z0-R .. z0-2) are free: the planes after z0+D
+#pragma unroll
+  for (int q = 0; q + 1 < R; ++q) issue(z0 + D + 1 + q, q);
+
+  int idx0 = z0 * plane + j * g.px + i;
+  const bool live = nx > 0 && j < N;
+  for (int kb = z0; kb < z1; kb += NB) {
+#pragma unroll
+    for (int uu = 0; uu < NB; ++uu) {
+      const int k = kb + uu;
+      if (k >= z1) break;  // uniform
+      const int sc = (uu + R) % NB;           // slot of plane k
+      const int sn = (uu + 2 * R) % NB;       // slot of plane k+R
+      const int sf = (uu + R + NB - 1) % NB;  // slot of plane k-1 (refilled)
+      typename Op::Ex4 ex;
+      if (live) ex = o.load4(idx0);
+      if (TMA) {
+        const bool ok = arrived(k + R, sn);
+        if (__syncthreads_or(!ok)) {
+          give_up(k + R + D - 1);
+          return;
+        }
+      } else {
+        cp_async_wait<D - 1>();
+        __syncthreads();
+      }
+      // plane k+R has arrived: its own points enter the queue and its
+      // boundary cells are completed (read as a current plane R iterations
+      // later, after a barrier); plane k-1 is no longer read (after the
+      // barrier), its slot takes plane k+R+D
+      qv[(uu + 2 * R) % QL] = own(sn);
+      if (k > z0) fill(k + R, sn);  // the prologue completed plane z0+R
+      issue(k + R + D, sf);
+      const float* P0 = ring + sc * PS + sbase;
+      const float4 cc = qv[(uu + R) % QL];
+      const float c[4] = {cc.x, cc.y, cc.z, cc.w};
+      // x: a[2..3] = x-2, x-1; a[4..7] = the four points; a[8..9] = x+4, x+5
+      float a[10];
+      if (R == 2) {
+        const float2 lh = *reinterpret_cast<const float2*>(P0 - 2);
+        const float2 rh = *reinterpret_cast<const float2*>(P0 + 4);
+        a[2] = lh.x; a[3] = lh.y; a[8] = rh.x; a[9] = rh.y;
+      } else {
+        a[2] = 0.f; a[3] = P0[-1]; a[8] = P0[4]; a[9] = 0.f;
+      }
+      a[4] = c[0]; a[5] = c[1]; a[6] = c[2]; a[7] = c[3];
+      const float4 ym1 = *reinterpret_cast<const float4*>(P0 - SX);
+      const float4 yp1 = *reinterpret_cast<const float4*>(P0 + SX);
+      const float4 zm1 = qv[(uu + R - 1) % QL], zp1 = qv[(uu + R + 1) % QL];
+      float xm1v[4], xp1v[4], ym1v[4] = {ym1.x, ym1.y, ym1.z, ym1.w}, yp1v[4] = {yp1.x, yp1.y, yp1.z, yp1.w};
+      float zm1v[4] = {zm1.x, zm1.y, zm1.z, zm1.w}, zp1v[4] = {zp1.x, zp1.y, zp1.z, zp1.w};
+      float xm2v[4] = {0.f, 0.f, 0.f, 0.f}, xp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float ym2v[4] = {0.f, 0.f, 0.f, 0.f}, yp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float zm2v[4] = {0.f, 0.f, 0.f, 0.f}, zp2v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xm1v[q] = a[3 + q];
+        xp1v[q] = a[5 + q];
+      }
+      if (R == 2) {
+        const float4 ym2 = *reinterpret_cast<const float4*>(P0 - 2 * SX);
+        const float4 yp2 = *reinterpret_cast<const float4*>(P0 + 2 * SX);
+        const float4 zm2 = qv[(uu + R - 2 + QL) % QL], zp2 = qv[(uu + R + 2) % QL];
+        ym2v[0] = ym2.x; ym2v[1] = ym2.y; ym2v[2] = ym2.z; ym2v[3] = ym2.w;
+        yp2v[0] = yp2.x; yp2v[1] = yp2.y; yp2v[2] = yp2.z; yp2v[3] = yp2.w;
+        zm2v[0] = zm2.x; zm2v[1] = zm2.y; zm2v[2] = zm2.z; zm2v[3] = zm2.w;
+        zp2v[0] = zp2.x; zp2v[1] = zp2.y; zp2v[2] = zp2.z; zp2v[3] = zp2.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          xm2v[q] = a[2 + q];
+          xp2v[q] = a[6 + q];
+        }
+      }
+      if (k < R || k >= N - R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(k, N, c[q], zm1v[q], zp1v[q], zm2v[q], zp2v[q]);
+      }
+      float s1[4], s2[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s1[q] = ((xm1v[q] + xp1v[q]) + (ym1v[q] + yp1v[q])) + (zm1v[q] + zp1v[q]);
+        s2[q] = R == 2 ? ((xm2v[q] + xp2v[q]) + (ym2v[q] + yp2v[q])) + (zm2v[q] + zp2v[q]) : 0.f;
+      }
+      if (live) o.apply4(idx0, nx, c, s1, s2, ex);
+      idx0 += plane;
+    }
+  }
+  if (!TMA) cp_async_wait<0>();
+}
+
+// The driver's tensor-map encoder, looked up once through the runtime (the
+// library does not link against the driver library itself).
+inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
+
+// zc > 0: planes per z-chunk; zc = -w: the chunk length for which the grid
+// fills w whole waves of the GPU (152 SMs x the blocks one SM holds).
+template <int ORDER, int TYT, int DEEP, int TMA, typename Op>
+cudaError_t launch_zq4(const Grid& g, int B, int zc, const int* active, const Op& op, cudaStream_t st) {
+  constexpr int smem = zq_smem<ORDER, TYT, DEEP>();
+  constexpr int R = ORDER == 4 ? 2 : 1;
+  auto kern = k_zq4<ORDER, TYT, DEEP, TMA, Op>;
+  if (smem > 48 * 1024) {
+    static std::atomic<bool> set{false};  // set once per process (one device)
+    if (!set.load()) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e != cudaSuccess) return e;
+      set.store(true);
+    }
+  }
+  const int tiles = ((g.N + 127) / 128) * ((g.N + TYT - 1) / TYT) * B;
+  if (zc <= 0) {
+    static std::atomic<int> slots{0};  // resident blocks on the whole GPU (one device)
+    if (slots.load() == 0) {
+      int dev = 0, sms = 0, bps = 0;
+      cudaError_t e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 32 * TYT, smem);
+      if (e != cudaSuccess) return e;
+      slots.store(std::max(1, sms * bps));
+    }
+    const int waves = zc < 0 ? -zc : 1;
+    const int nfit = std::max(1, waves * slots.load() / tiles);
+    zc = (g.N + nfit - 1) / nfit;
+  }
+  zc = std::min(zc, g.N);
+  const int nzc = (g.N + zc - 1) / zc;
+  CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  if (TMA) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    // dimensions x (pitch), y, z, item; the box is one plane of the tile with
+    // its halo, (128 + 8) x (TYT + 2R), starting at x0 - 4 (16-byte aligned)
+    const cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.N, (cuuint64_t)g.N, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.px * 4, (cuuint64_t)g.plane * 4,
+                                   (cuuint64_t)op.src_stride() * 4};
+    const cuuint32_t box[4] = {128 + 8, (cuuint32_t)(TYT + 2 * R), 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void*)op.src_base(), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  }
+  dim3 blk(32, TYT, 1);
+  dim3 grd((g.N + 127) / 128, (g.N + TYT - 1) / TYT, nzc * B);
+  kern<<<grd, blk, smem, st>>>(g, nzc, zc, active, op, map);
+  return cudaSuccess;
+}
+
 template <typename Op, typename = void>
 struct has_vec4 : std::false_type {};
 template <typename Op>
@@ -869,6 +1296,24 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
           default: e = launch_tile4<ORDER, 2, 2, 6>(g, B, nzc, zc, active, op, st); break;
         }
         break;
+      }
+      [[fallthrough]];
+    case 15: case 16: case 17: case 18: case 19: case 20: case 21: case 22:
+      if constexpr (has_vec4<Op>::value && !NORM && ORDER != kCompact) {
+        if (kind >= 15) {
+          const int zr = sh.zc;  // the launcher resolves wave-fitted chunks (zc < 0)
+          switch (kind) {
+            case 15: e = launch_zq4<ORDER, 8, 0, 0>(g, B, zr, active, op, st); break;
+            case 16: e = launch_zq4<ORDER, 4, 0, 0>(g, B, zr, active, op, st); break;
+            case 17: e = launch_zq4<ORDER, 8, 1, 0>(g, B, zr, active, op, st); break;
+            case 18: e = launch_zq4<ORDER, 16, 0, 0>(g, B, zr, active, op, st); break;
+            case 19: e = launch_zq4<ORDER, 8, 0, 1>(g, B, zr, active, op, st); break;
+            case 20: e = launch_zq4<ORDER, 4, 0, 1>(g, B, zr, active, op, st); break;
+            case 21: e = launch_zq4<ORDER, 8, 1, 1>(g, B, zr, active, op, st); break;
+            default: e = launch_zq4<ORDER, 16, 0, 1>(g, B, zr, active, op, st); break;
+          }
+          break;
+        }
       }
       [[fallthrough]];
     default: e = launch_tile<ORDER, 8, 2, 3, NORM>(g, B, nzc, zc, active, norm_bits, op, st); break;

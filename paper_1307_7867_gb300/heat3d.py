@@ -31,7 +31,8 @@ ABI_FUNCTIONS = [
     "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
     "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
     "heat3d_set_interval", "heat3d_kernel_launches", "heat3d_profile", "heat3d_profile_read",
-    "heat3d_selftest_barrier", "mg_vcycle_noalloc", "mg_vcycle_noalloc_last_error",
+    "heat3d_selftest_barrier", "heat3d_fp64_probe", "mg_vcycle_noalloc",
+    "mg_vcycle_noalloc_last_error",
     "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
     "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
 ]
@@ -127,6 +128,7 @@ def load():
     L.heat3d_profile.argtypes = [V, I]
     L.heat3d_profile_read.argtypes = [V, P(D), P(C.c_longlong), P(D), P(D), P(D)]
     L.heat3d_selftest_barrier.argtypes = [V, I]
+    L.heat3d_fp64_probe.argtypes = [V, P(D)]
     L.mg_vcycle_noalloc.argtypes = [I, I, I, D, V, V, I, D, V, P(Stats)]
     L.mg_vcycle_noalloc_last_error.argtypes = []
     L.mg_vcycle_noalloc_last_error.restype = C.c_char_p
@@ -305,6 +307,16 @@ def heat3d_profile_read(ctx: Context) -> dict:
             "flops": fl.value}
 
 
+def heat3d_fp64_probe(stream=None) -> float:
+    """FP64 FMAs per second of the current device (heat3d_fp64_probe)."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    v = C.c_double(0.0)
+    rc = load().heat3d_fp64_probe(sp, C.byref(v))
+    if rc != OK:
+        raise Heat3DError(rc, "FP64 probe failed")
+    return v.value
+
+
 def heat3d_selftest_barrier(absent_block, stream=None) -> int:
     """Return code of the bounded grid-barrier self-test (OK, or ETIMEOUT when
     block `absent_block` of the four stays away)."""
@@ -315,6 +327,10 @@ def heat3d_selftest_barrier(absent_block, stream=None) -> int:
 def mg_vcycle_noalloc(N, order, precision, c, rhs, u, max_cycles, tol, stream=None,
                       allow_notconv=False):
     """mg_vcycle without device allocation (static scratch inside the library, N <= 63)."""
+    for name, a in (("rhs", rhs), ("u", u)):
+        n = a.numel() if hasattr(a, "numel") else np.asarray(a).size
+        if n != int(N) ** 3:
+            raise ValueError(f"{name} holds {n} values, not N^3 = {int(N) ** 3}")
     st = Stats()
     sp = None
     if stream is not None:

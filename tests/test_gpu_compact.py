@@ -179,7 +179,7 @@ def test_compact_mixed_precision_matches_fp64_oracle(H, oracle):
     assert rel(uT, ref) <= 1e-9
 
 
-SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (10, 64)]
+SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (10, 64), (15, 8), (19, -1)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])

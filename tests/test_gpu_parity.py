@@ -348,13 +348,18 @@ def test_graphs_and_autotune_change_nothing(H, oracle, precision):
 
 
 SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (8, 2), (9, 16), (10, 64),
-          (11, 16), (12, 4), (13, 32), (14, 8)]
+          (11, 16), (12, 4), (13, 32), (14, 8), (15, 1), (15, 12), (16, 3), (16, 24), (17, 7),
+          (17, 64), (18, 5), (18, 16), (15, -1), (19, 1), (19, 12), (20, 3), (20, -1), (21, 7),
+          (21, 64), (22, 5), (22, -2)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_every_launch_shape_is_bitwise_identical(H, oracle, precision, monkeypatch):
     """Every stencil launch shape (z-march, the 32-wide tiles, the FP32
-    four-points-per-thread tiles) forced on all grids with N >= 16 gives
+    four-points-per-thread tiles, with the z neighbours in shared memory or
+    in registers, planes loaded by cp.async or by TMA; chunk lengths below,
+    at and above the register kernel's ring period, and wave-fitted) forced
+    on all grids with N >= 16 gives
     bitwise the result of the default shapes: PFASST with two slices batched
     (items in one launch), fine 127^3 (a ragged last x group of 3 points)."""
     fine, coarse = (127, 4, 3), (63, 2, 3)
@@ -475,3 +480,11 @@ def test_graph_replay_counts_launches_and_profile(H):
     prof = H.heat3d_profile_read(ctx)
     assert n1 - n0 > 10 * st["vcycles"]
     assert prof["launches"] == 2 * st["vcycles"] and prof["ms"] > 0
+
+
+def test_fp64_probe_reports_a_plausible_rate(H):
+    """The FP64 FMA probe (the FP64 stencils' roofline denominator) returns a
+    rate between 1e10 and 1e13 FMAs per second, repeatably within 10 %."""
+    a = H.heat3d_fp64_probe()
+    b = H.heat3d_fp64_probe()
+    assert 1e10 < a < 1e13 and abs(a - b) <= 0.1 * max(a, b)
