@@ -231,6 +231,7 @@ long long heat3d_kernel_launches(void);
 #define HEAT3D_PROF_OFF 0
 #define HEAT3D_PROF_JACOBI_FINE 1 /* damped-Jacobi sweeps on the finest multigrid level of SDC level 0 */
 #define HEAT3D_PROF_RESID64_FINE 2 /* FP64 refinement residual on SDC level 0 */
+#define HEAT3D_PROF_JACOBI_FINE_STORE 3 /* as 1, the sweeps that store the error (no FP64 update) */
 /* Brackets every launch of one kernel class with CUDA events on the context's
  * stream from now on (HEAT3D_PROF_OFF stops and clears). */
 int heat3d_profile(heat3d_ctx* ctx, int kernel_class);

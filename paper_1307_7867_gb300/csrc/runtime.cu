@@ -539,8 +539,15 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
     oth = cur == e ? t : e;
     first = 0;
   }
+  // profiled fine-level Jacobi launches: all of them, or those that store the
+  // error without the FP64 update
+  auto prof_jacobi = [&](bool upd) {
+    if (!prof_here) return -1;
+    const int pr = h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE);
+    return pr >= 0 || upd ? pr : h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE_STORE);
+  };
   for (int s = first; s < nu1; ++s) {
-    int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
+    int pr = prof_jacobi(false);
     CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
@@ -559,7 +566,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   c->bytes += ts * pts * (2.0 + 1.0 / 8.0);
   for (int s = 0; s < nu2; ++s) {
     const bool upd = k == 0 && final && s == nu2 - 1;
-    int pr = prof_here ? h3d_prof_begin(c, HEAT3D_PROF_JACOBI_FINE) : -1;
+    int pr = prof_jacobi(upd);
     if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, L.shapeT[k], st));
     else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
@@ -1631,7 +1638,7 @@ int heat3d_set_interval(heat3d_ctx* c, double t0, double T) {
 long long heat3d_kernel_launches(void) { return h3d::g_launches.load(); }
 
 int heat3d_profile(heat3d_ctx* c, int kernel_class) {
-  if (!c || kernel_class < 0 || kernel_class > HEAT3D_PROF_RESID64_FINE) return HEAT3D_EINVAL;
+  if (!c || kernel_class < 0 || kernel_class > HEAT3D_PROF_JACOBI_FINE_STORE) return HEAT3D_EINVAL;
   cudaStreamSynchronize(c->st);
   c->prof_used = 0;
   c->prof_ms = c->prof_bytes = c->prof_dpops = c->prof_flops = 0.0;

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libheat3d.so")
 
 OK, EINVAL, ENOMEM, ENOTCONV, ENAN, ETIMEOUT, ECUDA, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-PROF_OFF, PROF_JACOBI_FINE, PROF_RESID64_FINE = 0, 1, 2
+PROF_OFF, PROF_JACOBI_FINE, PROF_RESID64_FINE, PROF_JACOBI_FINE_STORE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 FORCING_NONE, FORCING_PAPER_LITERAL, FORCING_EXACT = 0, 1, 2
 COMPACT = 19  # heat3d_level.order of the compact 19-point (Mehrstellen) fine stencil
