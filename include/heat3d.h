@@ -259,6 +259,15 @@ int heat3d_selftest_barrier(void* stream, int absent_block);
  * HEAT3D_EINVAL for a NULL output, HEAT3D_ECUDA on a CUDA error. */
 int heat3d_fp64_probe(void* stream, double* fma_per_s);
 
+/* Self-test of the bounded mbarrier wait that the FP32 stencils' TMA plane
+ * loader uses (no counterpart in the paper): one block of 64 threads waits
+ * on a barrier that completes only if `arrive` is non-zero.  arrive != 0:
+ * HEAT3D_OK at once; arrive = 0: every wait gives up after about 1 s of SM
+ * clock cycles and the call returns HEAT3D_ETIMEOUT (the device stays
+ * usable).  Synchronises `stream` (a cudaStream_t; NULL: legacy); allocates
+ * no device memory; HEAT3D_ECUDA on a CUDA error. */
+int heat3d_selftest_mbarrier(void* stream, int arrive);
+
 /* ---------------------------------------------------------------------- */
 /* Solve without any device allocation (no counterpart in the paper).       */
 /* ---------------------------------------------------------------------- */

@@ -5,6 +5,7 @@
 // below 1, so the values stay bounded), enough warps per SM to hide the
 // pipe's latency; the result is FMAs per second over the timed launch.
 #include "runtime.cuh"
+#include "stencil_impl.cuh"
 
 namespace {
 
@@ -25,7 +26,41 @@ __global__ void __launch_bounds__(512) k_fp64_fma_probe(int iters, double a, dou
   if (s == -1.0) g_probe_sink = s;  // never true: keeps the chains live
 }
 
+// One block waits on an mbarrier with the bounded wait of the TMA plane
+// loader; the barrier completes only if `arrive` is set.  out = number of
+// threads whose wait gave up.
+__global__ void k_mbar_selftest(int arrive, int* out) {
+  __shared__ __align__(8) unsigned long long bar;
+  const unsigned b = (unsigned)__cvta_generic_to_shared(&bar);
+  if (threadIdx.x == 0) {
+    h3d::mbar_init(b, 1);
+    h3d::mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && arrive) h3d::mbar_arrive(b);
+  if (!h3d::mbar_wait_bounded(b, 0)) atomicAdd(out, 1);
+}
+
+__device__ int g_mbar_selftest_out;
+
 }  // namespace
+
+extern "C" int heat3d_selftest_mbarrier(void* stream, int arrive) {
+  cudaStream_t st = (cudaStream_t)stream;
+  int* out = nullptr;
+  if (cudaGetSymbolAddress((void**)&out, g_mbar_selftest_out) != cudaSuccess) return HEAT3D_ECUDA;
+  int failed = 0;
+  cudaError_t err = cudaMemsetAsync(out, 0, sizeof(int), st);
+  if (err == cudaSuccess) {
+    k_mbar_selftest<<<1, 64, 0, st>>>(arrive ? 1 : 0, out);
+    h3d::count_launch();
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemcpyAsync(&failed, out, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+  if (err != cudaSuccess) return HEAT3D_ECUDA;
+  return failed ? HEAT3D_ETIMEOUT : HEAT3D_OK;
+}
 
 extern "C" int heat3d_fp64_probe(void* stream, double* fma_per_s) {
   if (!fma_per_s) return HEAT3D_EINVAL;

@@ -1305,9 +1305,10 @@ static bool tune_log() {
 }
 
 // vec4: the operator has the four-points-per-thread FP32 tiles (kinds 7-14,
-// and 15-22 with the z neighbours in registers, 19-22 loading planes by
-// TMA); the latter also try a chunk of 12 planes and the chunks that fill
-// one or two whole waves of the GPU.
+// and 15-26 with the z neighbours in registers, 19-26 loading planes by
+// TMA, 23-26 with a producer warp and no block barriers); the latter also
+// try a chunk of 12 planes and the chunks that fill one or two whole waves
+// of the GPU.
 static std::vector<Shape> shape_candidates(int N, bool vec4) {
   std::vector<Shape> v;
   for (int zc : {1, 2, 4, 8, 16, 32, 64})
@@ -1317,7 +1318,7 @@ static std::vector<Shape> shape_candidates(int N, bool vec4) {
       for (int zc : {2, 4, 8, 16, 32, 64})
         if (zc <= N) v.push_back(Shape{kind, zc});
     if (vec4)  // zc -1, -2: the chunk length that fills one or two whole waves
-      for (int kind = 15; kind <= 22; ++kind)
+      for (int kind = 15; kind <= 26; ++kind)
         for (int zc : {8, 12, 16, 32, -1, -2})
           if (zc <= N) v.push_back(Shape{kind, zc});
   }
@@ -1616,7 +1617,7 @@ int heat3d_bind_workspace(heat3d_ctx* c, void* dptr, size_t bytes) {
   // every shape must give bitwise the same results)
   if (const char* f = getenv("HEAT3D_SHAPE")) {
     int kind = 0, zc = 0;
-    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 22 && zc >= -2 && zc != 0) {
+    if (sscanf(f, "%d,%d", &kind, &zc) == 2 && kind >= 1 && kind <= 26 && zc >= -2 && zc != 0) {
       for (int l = 0; l < c->cfg.nlevels; ++l) {
         SdcLevel& L = c->lv[l];
         for (int k = 0; k < L.nmg; ++k)

@@ -1187,6 +1187,211 @@ __global__ void __launch_bounds__(32 * TYT, (zq_min_blocks<ORDER, TYT, DEEP, zq_
   if (!TMA) cp_async_wait<0>();
 }
 
+// k_zq4 as a producer/consumer pipeline without block barriers: one extra
+// warp issues the TMA box of every plane once the ring slot it goes to has
+// been released, and each compute warp waits only for the slot's "full"
+// barrier and releases the slot (one arrival per warp on its "empty"
+// barrier) after its last read, so warps drift apart by up to the prefetch
+// depth instead of meeting at every plane.  The ring holds plain copies (the
+// out-of-domain cells read the TMA zero fill) and every boundary value is
+// set in registers: x at the two edge lanes, y for whole warps, z at the
+// edge planes.  Waits are bounded like k_zq4's; a warp that gives up sets
+// g_zq_timeout and returns, the producer then waits (bounded) for the copies
+// it issued.  The sums per point are those of k_tile4, so the results are
+// bitwise identical.
+template <int ORDER, int TYT, int DEEP>
+constexpr int zqp_min_blocks() {  // register floor 96: no spills in any variant
+  return (232448 / zq_smem<ORDER, TYT, DEEP>()) < (65536 / (32 * (TYT + 1) * 96))
+             ? (232448 / zq_smem<ORDER, TYT, DEEP>())
+             : (65536 / (32 * (TYT + 1) * 96));
+}
+
+template <int ORDER, int TYT, int DEEP, typename Op>
+__global__ void __launch_bounds__(32 * (TYT + 1), (zqp_min_blocks<ORDER, TYT, DEEP>()))
+    k_zq4p(Grid g, int nzc, int zc, const int* active, Op op, const __grid_constant__ CUtensorMap tmap) {
+  static_assert(sizeof(typename Op::T) == 4, "k_zq4p is the FP32 path");
+  static_assert(ORDER == 2 || ORDER == 4, "k_zq4p: 7-point and wide stencils");
+  constexpr int R = ORDER == 4 ? 2 : 1;
+  constexpr int D = zq_depth<ORDER, DEEP>();
+  constexpr int NB = R + D + 1;
+  constexpr int QL = 2 * R + 1;
+  static_assert(NB % QL == 0, "ring size must be a multiple of the queue length");
+  constexpr int TX = 128, TY = TYT, XH = 4;
+  constexpr int SX = TX + 2 * XH, SY = TY + 2 * R;
+  constexpr int PS = zq_slot_floats<ORDER, TYT>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long full[NB], empty[NB];
+  float* ring = reinterpret_cast<float*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  const int b = blockIdx.z / nzc;
+  if (active && !active[b]) return;  // uniform over the block
+  const int N = g.N;
+  const int plane = (int)g.plane;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int z0 = (blockIdx.z - b * nzc) * zc, z1 = min(N, z0 + zc);
+  const int warp = threadIdx.y, lane = threadIdx.x;
+  const unsigned ring_s = (unsigned)__cvta_generic_to_shared(ring);
+  const unsigned full_s = (unsigned)__cvta_generic_to_shared(full);
+  const unsigned empty_s = (unsigned)__cvta_generic_to_shared(empty);
+  if (warp == 0 && lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      mbar_init(full_s + 8u * q, 1);
+      mbar_init(empty_s + 8u * q, TYT);
+    }
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // fill f of the ring holds plane z0 - R + f in slot f mod NB; phase f / NB
+  // of that slot's barriers belongs to it
+  const int last = z1 - 1 + R;  // the last plane a compute warp reads
+  if (warp == TYT) {  // the producer
+    if (lane == 0) {
+      int f = 0;
+      bool ok = true;
+      for (; z0 - R + f <= last; ++f) {
+        const int p = z0 - R + f, s = f % NB;
+        if (f >= NB && !mbar_wait_bounded(empty_s + 8u * s, (unsigned)(f / NB - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        const unsigned bar = full_s + 8u * s;
+        if (p >= 0 && p < N) {
+          fence_proxy_async_smem();
+          mbar_expect_tx(bar, (unsigned)(SY * SX * 4));
+          tma_load_4d(ring_s + (unsigned)(s * PS) * 4u, &tmap, x0 - XH, y0 - R, p, b, bar);
+        } else {
+          mbar_arrive(bar);
+        }
+      }
+      if (!ok) {  // wait for the copies already issued, then leave
+        atomicExch(&g_zq_timeout, 1);
+        for (int q = f - 1; q >= 0 && q > f - 1 - NB; --q)
+          mbar_wait_bounded(full_s + 8u * (q % NB), (unsigned)(q / NB) & 1u);
+      }
+    }
+    return;
+  }
+
+  Op o = op;
+  o.init(b);
+  const int i = x0 + 4 * lane;
+  const int j = y0 + warp;
+  const int sbase = (R + warp) * SX + XH + 4 * lane;
+  const int nx = N - i;
+  auto own = [&](int slot) { return *reinterpret_cast<const float4*>(ring + slot * PS + sbase); };
+  auto wait_full = [&](int p) {
+    const int f = p - z0 + R;
+    return mbar_wait_bounded(full_s + 8u * (f % NB), (unsigned)(f / NB) & 1u);
+  };
+  auto release = [&](int slot) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_s + 8u * slot);
+  };
+  float4 qv[QL];
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < 2 * R; ++q) {
+    ok = wait_full(z0 - R + q) && ok;
+    qv[q] = own(q);
+  }
+  if (!ok) {
+    atomicExch(&g_zq_timeout, 1);
+    return;
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) release(q);  // planes z0-R .. z0-1 only feed the queue
+
+  int idx0 = z0 * plane + j * g.px + i;
+  const bool live = nx > 0 && j < N;
+  const bool yedge = j < R || j >= N - R;  // the same for the whole warp
+  for (int kb = z0; kb < z1; kb += NB) {
+#pragma unroll
+    for (int uu = 0; uu < NB; ++uu) {
+      const int k = kb + uu;
+      if (k >= z1) break;  // uniform
+      const int sc = (uu + R) % NB;      // slot of plane k
+      const int sn = (uu + 2 * R) % NB;  // slot of plane k+R
+      typename Op::Ex4 ex;
+      if (live) ex = o.load4(idx0);
+      if (!wait_full(k + R)) {
+        atomicExch(&g_zq_timeout, 1);
+        return;
+      }
+      qv[(uu + 2 * R) % QL] = own(sn);
+      const float* P0 = ring + sc * PS + sbase;
+      const float4 cc = qv[(uu + R) % QL];
+      const float c[4] = {cc.x, cc.y, cc.z, cc.w};
+      float a[10];
+      if (R == 2) {
+        const float2 lh = *reinterpret_cast<const float2*>(P0 - 2);
+        const float2 rh = *reinterpret_cast<const float2*>(P0 + 4);
+        a[2] = lh.x; a[3] = lh.y; a[8] = rh.x; a[9] = rh.y;
+      } else {
+        a[2] = 0.f; a[3] = P0[-1]; a[8] = P0[4]; a[9] = 0.f;
+      }
+      a[4] = c[0]; a[5] = c[1]; a[6] = c[2]; a[7] = c[3];
+      // x boundary: index -1 and N read 0, the wide stencil's ghosts -2 and
+      // N+1 minus the cell at 0 and N-1
+      if (i == 0) {
+        a[3] = 0.f;
+        if (R == 2) a[2] = -c[0];
+      }
+      if (nx > 0 && nx <= 4) {
+        const float cl = nx == 1 ? c[0] : nx == 2 ? c[1] : nx == 3 ? c[2] : c[3];
+#pragma unroll
+        for (int t = 5; t <= 9; ++t) {
+          if (t == 4 + nx) a[t] = 0.f;
+          if (R == 2 && t == 5 + nx) a[t] = -cl;
+        }
+      }
+      const float4 ym1 = *reinterpret_cast<const float4*>(P0 - SX);
+      const float4 yp1 = *reinterpret_cast<const float4*>(P0 + SX);
+      const float4 zm1 = qv[(uu + R - 1) % QL], zp1 = qv[(uu + R + 1) % QL];
+      float xm1v[4], xp1v[4], ym1v[4] = {ym1.x, ym1.y, ym1.z, ym1.w}, yp1v[4] = {yp1.x, yp1.y, yp1.z, yp1.w};
+      float zm1v[4] = {zm1.x, zm1.y, zm1.z, zm1.w}, zp1v[4] = {zp1.x, zp1.y, zp1.z, zp1.w};
+      float xm2v[4] = {0.f, 0.f, 0.f, 0.f}, xp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float ym2v[4] = {0.f, 0.f, 0.f, 0.f}, yp2v[4] = {0.f, 0.f, 0.f, 0.f};
+      float zm2v[4] = {0.f, 0.f, 0.f, 0.f}, zp2v[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        xm1v[q] = a[3 + q];
+        xp1v[q] = a[5 + q];
+      }
+      if (R == 2) {
+        const float4 ym2 = *reinterpret_cast<const float4*>(P0 - 2 * SX);
+        const float4 yp2 = *reinterpret_cast<const float4*>(P0 + 2 * SX);
+        const float4 zm2 = qv[(uu + R - 2 + QL) % QL], zp2 = qv[(uu + R + 2) % QL];
+        ym2v[0] = ym2.x; ym2v[1] = ym2.y; ym2v[2] = ym2.z; ym2v[3] = ym2.w;
+        yp2v[0] = yp2.x; yp2v[1] = yp2.y; yp2v[2] = yp2.z; yp2v[3] = yp2.w;
+        zm2v[0] = zm2.x; zm2v[1] = zm2.y; zm2v[2] = zm2.z; zm2v[3] = zm2.w;
+        zp2v[0] = zp2.x; zp2v[1] = zp2.y; zp2v[2] = zp2.z; zp2v[3] = zp2.w;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          xm2v[q] = a[2 + q];
+          xp2v[q] = a[6 + q];
+        }
+      }
+      release(sc);  // plane k's slot is read for the last time above
+      if (yedge) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(j, N, c[q], ym1v[q], yp1v[q], ym2v[q], yp2v[q]);
+      }
+      if (k < R || k >= N - R) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) fix_axis<float, R>(k, N, c[q], zm1v[q], zp1v[q], zm2v[q], zp2v[q]);
+      }
+      float s1[4], s2[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        s1[q] = ((xm1v[q] + xp1v[q]) + (ym1v[q] + yp1v[q])) + (zm1v[q] + zp1v[q]);
+        s2[q] = R == 2 ? ((xm2v[q] + xp2v[q]) + (ym2v[q] + yp2v[q])) + (zm2v[q] + zp2v[q]) : 0.f;
+      }
+      if (live) o.apply4(idx0, nx, c, s1, s2, ex);
+      idx0 += plane;
+    }
+  }
+}
+
 // The driver's tensor-map encoder, looked up once through the runtime (the
 // library does not link against the driver library itself).
 inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
@@ -1204,11 +1409,16 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
 
 // zc > 0: planes per z-chunk; zc = -w: the chunk length for which the grid
 // fills w whole waves of the GPU (152 SMs x the blocks one SM holds).
+// TMA = 0: k_zq4 with cp.async, 1: k_zq4 with TMA, 2: k_zq4p (TMA, producer
+// warp, no block barriers).
 template <int ORDER, int TYT, int DEEP, int TMA, typename Op>
 cudaError_t launch_zq4(const Grid& g, int B, int zc, const int* active, const Op& op, cudaStream_t st) {
   constexpr int smem = zq_smem<ORDER, TYT, DEEP>();
   constexpr int R = ORDER == 4 ? 2 : 1;
-  auto kern = k_zq4<ORDER, TYT, DEEP, TMA, Op>;
+  constexpr int threads = 32 * (TYT + (TMA == 2 ? 1 : 0));
+  void (*kern)(Grid, int, int, const int*, Op, const CUtensorMap);
+  if constexpr (TMA == 2) kern = k_zq4p<ORDER, TYT, DEEP, Op>;
+  else kern = k_zq4<ORDER, TYT, DEEP, TMA, Op>;
   if (smem > 48 * 1024) {
     static std::atomic<bool> set{false};  // set once per process (one device)
     if (!set.load()) {
@@ -1224,7 +1434,7 @@ cudaError_t launch_zq4(const Grid& g, int B, int zc, const int* active, const Op
       int dev = 0, sms = 0, bps = 0;
       cudaError_t e = cudaGetDevice(&dev);
       if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 32 * TYT, smem);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, threads, smem);
       if (e != cudaSuccess) return e;
       slots.store(std::max(1, sms * bps));
     }
@@ -1251,7 +1461,7 @@ cudaError_t launch_zq4(const Grid& g, int B, int zc, const int* active, const Op
                      CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
   }
-  dim3 blk(32, TYT, 1);
+  dim3 blk(32, threads / 32, 1);
   dim3 grd((g.N + 127) / 128, (g.N + TYT - 1) / TYT, nzc * B);
   kern<<<grd, blk, smem, st>>>(g, nzc, zc, active, op, map);
   return cudaSuccess;
@@ -1298,7 +1508,8 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
         break;
       }
       [[fallthrough]];
-    case 15: case 16: case 17: case 18: case 19: case 20: case 21: case 22:
+    case 15: case 16: case 17: case 18: case 19: case 20: case 21: case 22: case 23: case 24:
+    case 25: case 26:
       if constexpr (has_vec4<Op>::value && !NORM && ORDER != kCompact) {
         if (kind >= 15) {
           const int zr = sh.zc;  // the launcher resolves wave-fitted chunks (zc < 0)
@@ -1310,7 +1521,11 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
             case 19: e = launch_zq4<ORDER, 8, 0, 1>(g, B, zr, active, op, st); break;
             case 20: e = launch_zq4<ORDER, 4, 0, 1>(g, B, zr, active, op, st); break;
             case 21: e = launch_zq4<ORDER, 8, 1, 1>(g, B, zr, active, op, st); break;
-            default: e = launch_zq4<ORDER, 16, 0, 1>(g, B, zr, active, op, st); break;
+            case 22: e = launch_zq4<ORDER, 16, 0, 1>(g, B, zr, active, op, st); break;
+            case 23: e = launch_zq4<ORDER, 8, 1, 2>(g, B, zr, active, op, st); break;
+            case 24: e = launch_zq4<ORDER, 4, 1, 2>(g, B, zr, active, op, st); break;
+            case 25: e = launch_zq4<ORDER, 8, 0, 2>(g, B, zr, active, op, st); break;
+            default: e = launch_zq4<ORDER, 16, 0, 2>(g, B, zr, active, op, st); break;
           }
           break;
         }

@@ -31,7 +31,7 @@ ABI_FUNCTIONS = [
     "mg_vcycle", "heat3d_set_state", "heat3d_get_node", "heat3d_set_node", "sdc_sweep",
     "heat3d_sdc_residual", "heat3d_fas_restrict", "heat3d_fas_interpolate", "pfasst_run",
     "heat3d_set_interval", "heat3d_kernel_launches", "heat3d_profile", "heat3d_profile_read",
-    "heat3d_selftest_barrier", "heat3d_fp64_probe", "mg_vcycle_noalloc",
+    "heat3d_selftest_barrier", "heat3d_selftest_mbarrier", "heat3d_fp64_probe", "mg_vcycle_noalloc",
     "mg_vcycle_noalloc_last_error",
     "heat3d_server_create", "heat3d_submit", "heat3d_poll", "heat3d_wait",
     "heat3d_server_latency", "heat3d_server_destroy", "heat3d_server_last_error",
@@ -129,6 +129,7 @@ def load():
     L.heat3d_profile_read.argtypes = [V, P(D), P(C.c_longlong), P(D), P(D), P(D)]
     L.heat3d_selftest_barrier.argtypes = [V, I]
     L.heat3d_fp64_probe.argtypes = [V, P(D)]
+    L.heat3d_selftest_mbarrier.argtypes = [V, I]
     L.mg_vcycle_noalloc.argtypes = [I, I, I, D, V, V, I, D, V, P(Stats)]
     L.mg_vcycle_noalloc_last_error.argtypes = []
     L.mg_vcycle_noalloc_last_error.restype = C.c_char_p
@@ -315,6 +316,12 @@ def heat3d_fp64_probe(stream=None) -> float:
     if rc != OK:
         raise Heat3DError(rc, "FP64 probe failed")
     return v.value
+
+
+def heat3d_selftest_mbarrier(arrive, stream=None) -> int:
+    """Bounded mbarrier wait self-test: OK if the barrier completes, ETIMEOUT if not."""
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    return load().heat3d_selftest_mbarrier(sp, int(arrive))
 
 
 def heat3d_selftest_barrier(absent_block, stream=None) -> int:

@@ -350,14 +350,16 @@ def test_graphs_and_autotune_change_nothing(H, oracle, precision):
 SHAPES = [(1, 4), (2, 8), (3, 16), (4, 4), (5, 8), (6, 16), (7, 8), (8, 2), (9, 16), (10, 64),
           (11, 16), (12, 4), (13, 32), (14, 8), (15, 1), (15, 12), (16, 3), (16, 24), (17, 7),
           (17, 64), (18, 5), (18, 16), (15, -1), (19, 1), (19, 12), (20, 3), (20, -1), (21, 7),
-          (21, 64), (22, 5), (22, -2)]
+          (21, 64), (22, 5), (22, -2), (23, 1), (23, -1), (24, 3), (24, 37), (25, 2), (25, 16),
+          (26, 7), (26, -2)]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_every_launch_shape_is_bitwise_identical(H, oracle, precision, monkeypatch):
     """Every stencil launch shape (z-march, the 32-wide tiles, the FP32
     four-points-per-thread tiles, with the z neighbours in shared memory or
-    in registers, planes loaded by cp.async or by TMA; chunk lengths below,
+    in registers, planes loaded by cp.async or by TMA, with block barriers
+    or as a producer/consumer pipeline; chunk lengths below,
     at and above the register kernel's ring period, and wave-fitted) forced
     on all grids with N >= 16 gives
     bitwise the result of the default shapes: PFASST with two slices batched

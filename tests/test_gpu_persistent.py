@@ -161,3 +161,23 @@ def test_bounded_barrier_times_out_and_device_stays_usable(H):
     assert H.heat3d_selftest_barrier(-1, s) == H.OK
     x = torch.ones(1000, device="cuda")
     assert float(x.sum()) == 1000.0
+
+
+def test_bounded_mbarrier_wait_times_out_and_device_stays_usable(H):
+    """The bounded mbarrier wait of the FP32 stencils' TMA plane loader: a
+    barrier that nothing completes makes every waiting thread give up after
+    about a second; the call reports HEAT3D_ETIMEOUT and the device, and a
+    mixed-precision solve, keep working."""
+    import time
+    s = torch.cuda.Stream()
+    assert H.heat3d_selftest_mbarrier(1, s) == H.OK
+    t0 = time.perf_counter()
+    assert H.heat3d_selftest_mbarrier(0, s) == H.ETIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    assert H.heat3d_selftest_mbarrier(1, s) == H.OK
+    N = 63
+    ctx = H.Context(H.make_config((N, 4, 3), precision=H.MIXED))
+    b = inputs.random_field(N, seed=52)
+    u = torch.zeros(N, N, N, dtype=torch.float64, device="cuda")
+    rc, st = H.mg_vcycle(ctx, 0, 0.01, torch.from_numpy(b).cuda(), u, 50, 1e-12)
+    assert rc == H.OK and st["mg_residual"] <= 1e-12
