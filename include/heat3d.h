@@ -106,8 +106,9 @@ typedef struct {
                                stream) */
   int autotune;             /* 1: time the stencil launch shapes of every multigrid level at
                                heat3d_bind_workspace and keep the fastest (results identical).
-                               The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-14,
-                               planes per block zc) forces one shape on every stencil of
+                               The environment variable HEAT3D_SHAPE="kind,zc" (kind 1-26,
+                               planes per block zc, or -1 / -2 for the chunk that fills one /
+                               two waves of the GPU) forces one shape on every stencil of
                                grids with N >= 16 instead (testing); HEAT3D_TUNE_FILE=path
                                reuses the shapes recorded in that file for levels it lists
                                and appends the timed choices of the others */

@@ -4,7 +4,7 @@
 // and stencil order, with their launcher templates; stencil_f64.cu and
 // stencil_f32.cu instantiate them.
 //
-// Two drivers share one operator interface:
+// The drivers share one operator interface:
 //  * k_tile (grids with N >= 32): a block owns a 32 x TY tile of x-y points
 //    and marches along z through a chunk of planes.  The planes it needs
 //    (z-R .. z+R, R = 1 or 2) live in a shared-memory ring that cp.async
@@ -15,6 +15,10 @@
 //    replace those neighbours in registers (fix_axis).
 //  * k_tile4 (FP32 Jacobi and residual): as k_tile with four x points per
 //    thread and 16-byte shared and global accesses.
+//  * k_zq4 / k_zq4p (FP32 Jacobi and residual, 7-point and wide): as k_tile4
+//    with each thread's own points of the planes k-R .. k+R in a register
+//    queue; planes by cp.async or TMA (mbarrier per ring slot), k_zq4p as a
+//    producer/consumer pipeline without block barriers.
 //  * k_zmarch (small grids): one (x, y) column per thread, z-neighbours in a
 //    register queue, x/y neighbours through L1.
 // Boundary rule of every stencil read: indices -1 and N are the Dirichlet

@@ -48,3 +48,34 @@ def test_workload_config_names_the_solve_path_and_l2_regime():
     assert "fits in L2" in c1["l2"] and "no flush needed" in c2["l2"]
     off = bench.workload_config(dict(bench.WORKLOADS["c1"], persistent=0), 1)
     assert off["persistent_solves"] == "off"
+
+
+def test_stored_step_counts_come_from_the_oracle_script():
+    """The reference timing's per-step counts exist for the default workload
+    and are those of the oracle's own run (oracle/step_counts.py): the V-cycle
+    work over N_fine^3 lies between the fine V-cycles alone and all V-cycles."""
+    c2 = bench.stored_step_counts("c2")
+    assert c2 is not None and c2["status"] == 0 and c2["steps"] >= 1
+    fine_equiv = c2["vcycle_points_per_step"] / 255.0**3
+    assert 0 < fine_equiv < c2["vcycles_per_step"]
+    assert c2["iters_per_step"] >= 1
+    assert bench.stored_step_counts("no-such-workload") is None
+
+
+def test_reference_arm_without_counts_reports_unavailable():
+    import argparse
+    a = argparse.Namespace(steps=1, warmup=0)
+    out = bench.run_reference(a, bench.WORKLOADS["c3"], "c3")
+    assert out["impl"] == "reference" and "unavailable" in out
+
+
+def test_host_info_names_threads_and_cpu():
+    cores, model = bench.host_info()
+    assert cores >= 1 and isinstance(model, str) and model
+
+
+def test_mixed_inner_follows_the_tolerance_rule(monkeypatch):
+    monkeypatch.delenv("HEAT3D_INNER", raising=False)
+    assert bench.mixed_inner() == 3 and bench.mixed_inner(0.02) == 2
+    monkeypatch.setenv("HEAT3D_INNER", "5")
+    assert bench.mixed_inner() == 5
