@@ -150,6 +150,9 @@ static heat3d_config group_config(const heat3d_server* s, int N, cudaStream_t st
   c.slices = 1;
   c.device = s->cfg.device;
   c.stream = st;
+  // V-cycles replayed from CUDA graphs with the stop rule on the device (one
+  // graph per substep and number of resident requests, captured on first use)
+  c.use_graphs = 1;
   return c;
 }
 
