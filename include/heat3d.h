@@ -74,7 +74,10 @@ typedef struct {
   int max_cycles; /* cap per solve, counted in refinement steps */
   double tol;     /* stop when max|b - A u| <= tol; tol < 0: exactly max_cycles cycles */
   int inner;      /* V-cycles per refinement step (per FP64 residual), >= 1; the
-                     tolerance is checked after each step */
+                     tolerance is checked after each step.  0 with HEAT3D_MIXED: chosen
+                     per step (1-4) from the residuals seen so far and the contraction
+                     per V-cycle of the previous step, with graph replay (use_graphs);
+                     3 on the other paths */
   double rel;     /* > 0 (with tol >= 0): inside an SDC sweep, item b's solves stop at
                      max(tol, rel * r_b), r_b = the collocation residual of the sweep's
                      incoming iterate (the paper leaves the solver tolerance open);

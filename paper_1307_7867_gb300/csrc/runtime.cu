@@ -618,9 +618,10 @@ static bool graphs_usable(heat3d_ctx* c) {
 }
 
 static CycleGraph* find_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* u,
-                              const double* rhs) {
+                              const double* rhs, int inner) {
   for (CycleGraph* g : c->graphs)
-    if (g->lev == lev && g->slot == slot && g->b0 == b0 && g->B == B && g->u == u && g->rhs == rhs)
+    if (g->lev == lev && g->slot == slot && g->b0 == b0 && g->B == B && g->u == u && g->rhs == rhs &&
+        g->inner == inner)
       return g;
   return nullptr;
 }
@@ -654,9 +655,9 @@ static void graph_harvest(heat3d_ctx* c, CycleGraph* g) {
 // launches and bytes it enqueues are recorded per replay instead of now.
 template <typename Fn>
 static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const double* u,
-                         const double* rhs, Fn& fn, CycleGraph** out) {
+                         const double* rhs, int inner, Fn& fn, CycleGraph** out) {
   CycleGraph* g = new CycleGraph();
-  g->lev = lev; g->slot = slot; g->b0 = b0; g->B = B; g->u = u; g->rhs = rhs;
+  g->lev = lev; g->slot = slot; g->b0 = b0; g->B = B; g->u = u; g->rhs = rhs; g->inner = inner;
   g->prof_class = c->prof_class;
   const long long l0 = h3d::launches_total();
   const double by0 = c->bytes;
@@ -692,10 +693,12 @@ static int capture_graph(heat3d_ctx* c, int lev, int slot, int b0, int B, const 
 
 // Stats and return code of a solve whose stop rule ran on the device: per
 // item the cycles done, the last residual norm and its tolerance.
+// vcycles >= 0: the V-cycles done when the refinement steps did not all
+// take `inner` of them.
 static int solve_outcome(heat3d_ctx* c, int lev, int B, int inner, bool fixed, double tol,
                          int max_cycles, const std::vector<double>& tl,
                          const std::vector<int>& hcyc, const std::vector<double>& last, int nan,
-                         heat3d_stats* s) {
+                         heat3d_stats* s, long long vcycles = -1) {
   if (nan) return h3d_fail(c, HEAT3D_ENAN, "NaN/Inf residual in a multigrid solve");
   long long total = 0;
   double mx = 0;
@@ -705,9 +708,10 @@ static int solve_outcome(heat3d_ctx* c, int lev, int B, int inner, bool fixed, d
     mx = std::max(mx, last[b]);
     if (!fixed && !(last[b] <= tl[b])) ++notconv;
   }
+  if (vcycles < 0) vcycles = total * inner;
   if (s) {
-    s->vcycles += total * inner;
-    s->vcycles_level[lev] += total * inner;
+    s->vcycles += vcycles;
+    s->vcycles_level[lev] += vcycles;
     s->solves += B;
     s->mg_residual = mx;
   }
@@ -777,7 +781,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
     return HEAT3D_OK;
   };
-  const int inner = std::max(1, c->cfg.mg.inner);
+  // inner = 0 (mixed precision): the number of FP32 V-cycles per FP64
+  // residual is chosen per refinement step on the host from the residuals
+  // seen so far (graph path, one step per replay); the other paths take 3.
+  const bool adaptive = c->cfg.mg.inner == 0 && sizeof(T) == 4;
+  const int inner = adaptive ? 3 : std::max(1, c->cfg.mg.inner);
   if (L.persist) {
     // the whole solve in one persistent kernel (same cycles and results)
     std::vector<double> tl(B);
@@ -828,10 +836,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
                 (16.0 + 2.0 * sizeof(T)) * pts;
     return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hnan, s);
   }
+  int nin = inner;  // V-cycles of the next refinement step
   auto one_cycle = [&]() -> int {
     T* cur = nullptr;
-    for (int q = 0; q < inner; ++q)
-      RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &cur, q > 0, q == inner - 1));
+    for (int q = 0; q < nin; ++q)
+      RET(vcycle_level<T>(c, L, slot, 0, b0, B, act, u, us, &cur, q > 0, q == nin - 1));
     return residual();
   };
   if (graphs_usable(c)) {
@@ -840,7 +849,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     // cycles skip them), and the host synchronises once per chunk of cycles:
     // the same cycles as checking after each one.  Small grids take chunks
     // of 4 (their cycles are short against a host round trip), large grids 1.
-    const int chunk = g.N >= 127 ? 1 : 4;
+    const int chunk = g.N >= 127 || adaptive ? 1 : 4;
     std::vector<double> tl(B);
     for (int b = 0; b < B; ++b) tl[b] = fixed ? -1.0 : (tolv ? tolv[b] : tol);
     const int hdr[2] = {0, max_cycles};
@@ -858,23 +867,53 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
       }
       return HEAT3D_OK;
     };
-    CycleGraph* gph = find_graph(c, lev, slot, b0, B, u, rhs);
-    if (gph && gph->prof_class != c->prof_class) {
-      drop_graph(c, gph);
-      gph = nullptr;
-    }
-    if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, chunk_fn, &gph));
     std::vector<int> hact(B), hcyc(B, 0), prev(B, 0);
+    std::vector<double> lastv(B), lastp(B);
+    // adaptive: the worst active item's residual over its tolerance, and the
+    // contraction per FP32 V-cycle seen in the previous step (start 0.2)
+    double rho = 0.2;
+    if (adaptive) {
+      CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(lastv.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
     int launched = 0;
+    long long vdone = 0;
     for (;;) {
+      if (adaptive) {
+        double q = 1.0;
+        for (int b = 0; b < B; ++b)
+          if (hact[b] && tl[b] > 0) q = std::max(q, lastv[b] / tl[b]);
+        // cycles to reach the tolerance at the observed contraction, 1 to 4
+        // (an FP32 error equation gains about 6 digits per refinement step)
+        const double need = std::log(std::min(q, 1e6)) / -std::log(rho);
+        nin = std::max(1, std::min(4, (int)std::ceil(need - 1e-9)));
+        lastp = lastv;
+      }
+      CycleGraph* gph = find_graph(c, lev, slot, b0, B, u, rhs, nin);
+      if (gph && gph->prof_class != c->prof_class) {
+        drop_graph(c, gph);
+        gph = nullptr;
+      }
+      if (!gph) RET(capture_graph(c, lev, slot, b0, B, u, rhs, nin, chunk_fn, &gph));
       CK(cudaGraphLaunch(gph->exec, st));
       h3d::launches_adjust(gph->launches);
       launched += chunk;
       CK(cudaMemcpyAsync(hact.data(), act, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(hcyc.data(), L.mg_ncyc + b0, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+      if (adaptive)
+        CK(cudaMemcpyAsync(lastv.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       long long done = 0;
       for (int b = 0; b < B; ++b) done += hcyc[b] - prev[b];
+      vdone += done * nin;
+      if (adaptive) {  // worst contraction per V-cycle of the items that took this step
+        double worst = 0.0;
+        for (int b = 0; b < B; ++b)
+          if (hcyc[b] > prev[b] && lastp[b] > 0 && lastv[b] <= 1e300)
+            worst = std::max(worst, std::pow(lastv[b] / lastp[b], 1.0 / nin));
+        if (worst > 0) rho = std::min(0.7, std::max(0.02, worst));
+      }
       prev = hcyc;
       // work of this replay: item-cycles done out of chunk * B launched
       c->work_scale = (double)done / ((double)chunk * B);
@@ -890,7 +929,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     CK(cudaMemcpyAsync(last.data(), L.mg_last + b0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(hflag, L.mg_flag, sizeof(hflag), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hflag[0], s);
+    return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hflag[0], s, vdone);
   }
   RET(residual());
   int cycles = 0, live = B;

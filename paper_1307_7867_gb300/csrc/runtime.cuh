@@ -72,6 +72,7 @@ struct SdcLevel {
 // residual, device-side stop rule) for one solve key.
 struct CycleGraph {
   int lev = 0, slot = 0, b0 = 0, B = 0;
+  int inner = 1;  // V-cycles per refinement step in this graph
   const double* u = nullptr;
   const double* rhs = nullptr;
   cudaGraphExec_t exec = nullptr;

@@ -321,6 +321,30 @@ def test_run_mixed_precision_matches_fp64_oracle(H, oracle):
     assert rel(uT, ref) <= 1e-9
 
 
+def test_adaptive_fp32_cycles_per_refinement_match_fp64_oracle(H, oracle):
+    """Mixed precision with the number of FP32 V-cycles per FP64 residual
+    chosen per refinement step (inner = 0, graph replay, launch sequence):
+    the MLSDC result stays within 1e-9 of the FP64 oracle at the same
+    residual threshold, with no more V-cycles than 3 per step would take."""
+    fine, coarse = (31, 4, 5), (15, 2, 3)
+    outs = {}
+    for inner in (0, 3):
+        cfg = H.make_config(fine, coarse, dt=1 / 32, T=2 / 32, precision=H.MIXED, mg_tol=1e-11,
+                            inner=inner, use_graphs=1, persistent=0)
+        ctx = H.Context(cfg, stream=torch.cuda.Stream())
+        u0 = inputs.sine_mode(31)
+        uT = np.empty_like(u0)
+        rc, st = H.pfasst_run(ctx, u0, uT)
+        outs[inner] = (uT, st)
+        ctx.close()
+    ref, _, _ = oracle.mlsdc_run(fine, coarse, oracle.Prob(mg_tol=1e-11), 1 / 32, 2, inputs.sine_mode(31),
+                                 nsweeps_fine=2, max_iters=20, tol=1e-10)
+    uT, st = outs[0]
+    assert rel(uT, ref) <= 1e-9
+    assert st["residual"] <= 1e-10
+    assert st["vcycles"] <= outs[3][1]["vcycles"]
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_graphs_and_autotune_change_nothing(H, oracle, precision):
     """V-cycles replayed from CUDA graphs (private stream), autotuned launch
