@@ -904,7 +904,8 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_configs and args.workload == "c2":
         # the other configurations of the scope table, each with its own
-        # timed region, clocks and roofline; a failure is recorded in its entry
+        # timed region, clocks and roofline, and the speedup model; a failure
+        # is recorded in its entry
         # c3 with the 8-point rule also iterated to convergence, and the
         # paper's own setup (32 slices of dt = 0.1875, its compact fine
         # stencil, mixed precision; one block of slices as warm-up)
@@ -925,6 +926,14 @@ def main():
                                             "clocks")}
         except Exception as exc:  # noqa: BLE001
             out["c5"] = {"error": str(exc)[:300]}
+        # the speedup model of Sec. 1.1 with the 8-point correction interpolation
+        try:
+            import copy
+            a8 = copy.copy(args)
+            a8.interp = 8
+            out["alpha_p8"] = run_alpha(a8)
+        except Exception as exc:  # noqa: BLE001
+            out["alpha_p8"] = {"error": str(exc)[:300]}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         K = max(args.steps, 1)
