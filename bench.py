@@ -668,7 +668,8 @@ def run_serving(args):
     pool = torch.empty(int(args.pool_gb * 2**30), dtype=torch.uint8, device="cuda")
 
     def serve(reqs, rate):
-        srv = H.Server(pool, max_active=16, sweeps=4, precision=H.MIXED, mg_tol=1e-10, inner=2)
+        srv = H.Server(pool, max_active=16, sweeps=4, precision=H.MIXED, mg_tol=1e-10,
+                       inner=mixed_inner())
         tickets = [None] * len(reqs)
         t0 = time.perf_counter()
 
@@ -716,6 +717,7 @@ def run_serving(args):
                                    "{0.25,0.5,1}, 8 seeded sine modes, zero forcing, 3-node SDC, "
                                    "7-point, dt=1/32, 4 sweeps/step, FP32 V-cycles in FP64 "
                                    "refinement to 1e-10, 16 slots per grid size",
+                       "inner": mixed_inner(),
                        "requests": n, "arrival_rate_rps": rate},
             "latency": {"p50_s": lo["p50_s"], "p99_s": lo["p99_s"], "completed": lo["completed"]},
             "saturation": {"value": sat["value"], "makespan_s": sat["makespan_s"],

@@ -76,8 +76,8 @@ typedef struct {
   int inner;      /* V-cycles per refinement step (per FP64 residual), >= 1; the
                      tolerance is checked after each step.  0 with HEAT3D_MIXED: chosen
                      per step (1-4) from the residuals seen so far and the contraction
-                     per V-cycle of the previous step, with graph replay (use_graphs);
-                     3 on the other paths */
+                     per V-cycle of the previous step, with graph replay (use_graphs)
+                     and tol >= 0; 3 on the other paths */
   double rel;     /* > 0 (with tol >= 0): inside an SDC sweep, item b's solves stop at
                      max(tol, rel * r_b), r_b = the collocation residual of the sweep's
                      incoming iterate (the paper leaves the solver tolerance open);

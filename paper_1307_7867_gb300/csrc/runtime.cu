@@ -781,10 +781,11 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
     return HEAT3D_OK;
   };
-  // inner = 0 (mixed precision): the number of FP32 V-cycles per FP64
-  // residual is chosen per refinement step on the host from the residuals
-  // seen so far (graph path, one step per replay); the other paths take 3.
-  const bool adaptive = c->cfg.mg.inner == 0 && sizeof(T) == 4;
+  // inner = 0 (mixed precision, tolerance solves): the number of FP32
+  // V-cycles per FP64 residual is chosen per refinement step on the host from
+  // the residuals seen so far (graph path, one step per replay); the other
+  // paths and fixed-count solves take 3.
+  const bool adaptive = c->cfg.mg.inner == 0 && sizeof(T) == 4 && tol >= 0;
   const int inner = adaptive ? 3 : std::max(1, c->cfg.mg.inner);
   if (L.persist) {
     // the whole solve in one persistent kernel (same cycles and results)
