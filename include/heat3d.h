@@ -287,9 +287,12 @@ int heat3d_selftest_mbarrier(void* stream, int arrive);
  *  - rhs, u: host or device, dense N^3 FP64; u is the warm start and result.
  *  - Runs on the current device and `stream`.  Every call is synchronous:
  *    it waits for `stream` to finish before it returns, with u complete
- *    (host buffers are read and written on that stream).
+ *    (host buffers are read and written on that stream).  So it can never be
+ *    captured into a CUDA graph: called while `stream` (NULL: the legacy
+ *    stream) is being captured it returns HEAT3D_EINVAL at once, without
+ *    touching the stream, and the capture stays valid.
  *  - The first call on a device looks up the array's device address and sets
- *    up the solver state: make it before any stream capture.
+ *    up the solver state.
  *  - Calls share the array (it keeps the last call's contents; the solver
  *    clears what must start at zero).  Calls that overlap on the GPU race:
  *    serialise them.  stats->seconds is not measured (0).

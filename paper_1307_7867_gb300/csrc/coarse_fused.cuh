@@ -100,42 +100,45 @@ __device__ __forceinline__ void vcycle_small_body(const SmallArgs<T>& a, int ite
   __syncthreads();
   T* cur[kMaxLevels];
   T* oth[kMaxLevels];
-  // down: pre-smoothing, residual, restriction
+  // down: pre-smoothing from the scaled right-hand side b' (the first
+  // iterate, never written), residual, restriction
   for (int l = 0; l < a.nlev; ++l) {
     const int N = a.N[l];
     const Coef<T> c = a.cf[l][item];
     const int n3 = N * N * N;
     if (N == 1) {
-      if (tid == 0) le[l][0] = lb[l][0] / c.a11;
+      if (tid == 0) le[l][0] = lb[l][0] / c.a11w;
       cur[l] = le[l];
       __syncthreads();
       break;
     }
-    for (int q = tid; q < n3; q += nt) le[l][q] = c.wd * lb[l][q];
-    __syncthreads();
-    T* cu = le[l];
-    T* ot = lt[l];
+    T* cu = lb[l];
+    T* ot = le[l];
     for (int s = 1; s < a.nu1; ++s) {
       for (int q = tid; q < n3; q += nt) {
         const int i = q % N, j = (q / N) % N, k = q / (N * N);
         T s1, s2;
         nsums<T, ORDER>(cu, N, i, j, k, s1, s2);
-        const T cc = cu[q];
-        const T res = fma(-c.d, cc, fma(c.e, combine_s<T, ORDER>(s1, s2), lb[l][q]));
-        ot[q] = fma(c.wd, res, cc);
+        ot[q] = fma(c.al, cu[q], fma(c.be, combine_s<T, ORDER>(s1, s2), lb[l][q]));
       }
       __syncthreads();
-      T* tmp = cu; cu = ot; ot = tmp;
+      if (cu == lb[l]) {
+        cu = ot;
+        ot = lt[l];
+      } else {
+        T* tmp = cu; cu = ot; ot = tmp;
+      }
     }
     for (int q = tid; q < n3; q += nt) {
       const int i = q % N, j = (q / N) % N, k = q / (N * N);
       T s1, s2;
       nsums<T, ORDER>(cu, N, i, j, k, s1, s2);
-      ot[q] = fma(-c.d, cu[q], fma(c.e, combine_s<T, ORDER>(s1, s2), lb[l][q]));
+      ot[q] = fma(-c.om, cu[q], fma(c.be, combine_s<T, ORDER>(s1, s2), lb[l][q]));
     }
     __syncthreads();
-    // full weighting into the next level's right-hand side
+    // full weighting into the next level's scaled right-hand side
     const int Nc = a.N[l + 1];
+    const T rs = a.cf[l + 1][item].rs;
     const T w[3] = {T(0.25), T(0.5), T(0.25)};
     for (int q = tid; q < Nc * Nc * Nc; q += nt) {
       const int I = q % Nc, J = (q / Nc) % Nc, K = q / (Nc * Nc);
@@ -147,19 +150,21 @@ __device__ __forceinline__ void vcycle_small_body(const SmallArgs<T>& a, int ite
           const T* row = ot + ((fk + cz) * N + (fj + cy)) * N + fi;
           for (int cx = -1; cx <= 1; ++cx) sacc = fma(wcb * w[cx + 1], row[cx], sacc);
         }
-      lb[l + 1][q] = sacc;
+      lb[l + 1][q] = sacc * rs;
     }
     cur[l] = cu;
     oth[l] = ot;
     __syncthreads();
   }
-  // up: prolongation (cell-based, as k_prolong_add) and post-smoothing
+  // up: prolongation (cell-based, as k_prolong_add; from b' into the free
+  // buffer when no pre-smoothing sweep ran) and post-smoothing
   for (int l = a.nlev - 2; l >= 0; --l) {
     const int N = a.N[l], Nc = a.N[l + 1];
     const Coef<T> c = a.cf[l][item];
     const T* ec = cur[l + 1];
     T* cu = cur[l];
     T* ot = oth[l];
+    T* dst = cu == lb[l] ? ot : cu;
     const int nc1 = Nc + 1;
     for (int q = tid; q < nc1 * nc1 * nc1; q += nt) {
       const int cx = q % nc1, cy = (q / nc1) % nc1, cz = q / (nc1 * nc1);
@@ -194,22 +199,24 @@ __device__ __forceinline__ void vcycle_small_body(const SmallArgs<T>& a, int ite
             T wv = mz == 0 ? Y[0][my][mx] + Y[1][my][mx] : Y[1][my][mx];
             const int na = (mx == 0) + (my == 0) + (mz == 0);
             const T val = na == 0 ? wv : wv * (na == 1 ? T(0.5) : na == 2 ? T(0.25) : T(0.125));
-            T* o = cu + (fz * N + fy) * N + fx;
-            *o = *o + val;
+            const int o = (fz * N + fy) * N + fx;
+            dst[o] = cu[o] + val;
           }
         }
       }
     }
     __syncthreads();
+    if (cu == lb[l]) {
+      cu = dst;
+      ot = dst == le[l] ? lt[l] : le[l];
+    }
     const int n3 = N * N * N;
     for (int s = 0; s < a.nu2; ++s) {
       for (int q = tid; q < n3; q += nt) {
         const int i = q % N, j = (q / N) % N, k = q / (N * N);
         T s1, s2;
         nsums<T, ORDER>(cu, N, i, j, k, s1, s2);
-        const T cc = cu[q];
-        const T res = fma(-c.d, cc, fma(c.e, combine_s<T, ORDER>(s1, s2), lb[l][q]));
-        ot[q] = fma(c.wd, res, cc);
+        ot[q] = fma(c.al, cu[q], fma(c.be, combine_s<T, ORDER>(s1, s2), lb[l][q]));
       }
       __syncthreads();
       T* tmp = cu; cu = ot; ot = tmp;

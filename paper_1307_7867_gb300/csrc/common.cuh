@@ -38,9 +38,16 @@ inline Grid make_grid(int N) {
 //   compact stencil: A u = d u - e S1 - e2 S2 with S1 the 6 face and S2 the
 //   12 edge neighbours (W - c L of the Mehrstellen scheme);
 //   wd = omega / d for damped Jacobi; a11 = A on the one-unknown grid.
+// The V-cycle keeps every level's right-hand side scaled, b' = wd b (it is
+// also the first Jacobi iterate from zero), so that a sweep is
+//   v = al u + be S + b'          (al = 1 - omega, be = wd e; compact: + be2 S2)
+// and the residual it restricts is t' = wd (b - A u) = b' - om u + be S
+// (om = omega); the restriction into level k multiplies by rs = wd_k / wd_{k-1},
+// and the one-unknown grid solves e = b' / a11w (a11w = wd a11).
 template <typename T>
 struct Coef {
   T d, e, wd, a11, e2;
+  T al, om, be, be2, rs, a11w;
 };
 
 // Order code of the compact 19-point (Mehrstellen) stencil.

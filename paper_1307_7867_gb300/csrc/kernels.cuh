@@ -39,45 +39,52 @@ cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long lo
                        const int* active, Shape sh, cudaStream_t st, double* wu_out = nullptr);
 
 // ---- multigrid pieces (Sec. 1.2) ----
-// r = b - A u (FP64), written as TR into r_out; e0_out = wd * r (optional);
-// norm_bits[b] = max(norm_bits[b], bits of max|r|) (optional).
+// r = b - A u (FP64); bp_out = wd (TR) r, the scaled right-hand side of the
+// error equation and the first Jacobi iterate (the V-cycle's levels hold
+// b' = wd b, see Coef); norm_bits[b] = max(norm_bits[b], bits of max|r|)
+// (optional).
 template <typename TR>
 cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, long long u_stride,
                            const double* b, long long b_stride, const Coef<double>* coef,
-                           TR* r_out, TR* e0_out, const Coef<TR>* coef_r,
+                           TR* bp_out, const Coef<TR>* coef_r,
                            unsigned long long* norm_bits, const int* active, Shape sh,
                            cudaStream_t st);
 
-// Damped Jacobi: out = e + wd (r - A e).  With u64 != nullptr the result is
-// added to u64 (u64 += out) instead of being stored in out.
 // Reads and clears the FP32 tile's lost-copy flag (synchronises the stream).
 cudaError_t loader_timeouts_take(cudaStream_t st, int* flag);
+
+// Damped Jacobi with the scaled right-hand side r = b' = wd b:
+// out = e + wd (b - A e) = al e + be S (+ be2 S2) + b'.  With u64 != nullptr
+// the result is added to u64 (u64 += out) instead of being stored in out.
 
 template <typename T>
 cudaError_t launch_jacobi(int order, const Grid& g, int B, const T* e, const T* r, T* out,
                           double* u64, long long u64_stride, const Coef<T>* coef,
                           const int* active, Shape sh, cudaStream_t st);
 
-// rr = r - A e
+// rr = t' = wd (b - A e) = r - om e + be S (+ be2 S2), r = b' = wd b
 template <typename T>
 cudaError_t launch_resid(int order, const Grid& g, int B, const T* e, const T* r, T* rr,
                          const Coef<T>* coef, const int* active, Shape sh, cudaStream_t st);
 
-// e = wd * r (Jacobi from a zero initial guess); on a one-unknown grid
-// e = r / a11 (exact coarsest solve) when `exact` is set.
+// Exact solve on a one-unknown grid from the scaled right-hand side:
+// e = r / a11w (= b / a11).
 template <typename T>
-cudaError_t launch_jacobi_zero(const Grid& g, int B, const T* r, T* e, const Coef<T>* coef,
-                               bool exact, const int* active, cudaStream_t st);
+cudaError_t launch_solve_one(const Grid& g, int B, const T* r, T* e, const Coef<T>* coef,
+                             const int* active, cudaStream_t st);
 
-// Full weighting: bc (coarse grid gc) <- FW(rr) (fine grid gf, N_f = 2 N_c + 1).
+// Full weighting of the scaled residual into the coarse level's scaled
+// right-hand side: bc (coarse grid gc) <- rs * FW(rr) (fine grid gf,
+// N_f = 2 N_c + 1; rs from the coarse level's coefficients cc).
 template <typename T>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, int B, const T* rr, T* bc,
-                            const int* active, cudaStream_t st);
+                            const Coef<T>* cc, const int* active, cudaStream_t st);
 
-// Trilinear prolongation: uf += P ec.
+// Trilinear prolongation: uf = src + P ec (src may be uf: uf += P ec; both at
+// the item stride uf_stride).
 template <typename T>
 cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* ec,
-                               long long ec_stride, T* uf, long long uf_stride,
+                               long long ec_stride, const T* src, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st);
 
 // uf += tensor-product npts-point midpoint interpolation of ec (the FAS

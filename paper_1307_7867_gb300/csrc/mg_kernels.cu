@@ -46,22 +46,22 @@ inline dim3 point_grid(const Grid& g, int B) {
   return dim3((g.N + 31) / 32, (g.N + 7) / 8, g.N * B);
 }
 
+// The one-unknown grid's exact solve from the scaled right-hand side.
 template <typename T>
-__global__ void k_jacobi_zero(Grid g, const T* __restrict__ r, T* __restrict__ e,
-                              const Coef<T>* coef, int exact, const int* active) {
+__global__ void k_solve_one(Grid g, const T* __restrict__ r, T* __restrict__ e,
+                            const Coef<T>* coef, const int* active) {
   PointIdx p;
   if (!point_index(g, p)) return;
   if (active && !active[p.b]) return;
   long long o = p.b * g.fs + p.idx;
-  if (exact) e[o] = r[o] / coef[p.b].a11;
-  else e[o] = coef[p.b].wd * r[o];
+  e[o] = r[o] / coef[p.b].a11w;
 }
 
 // Full weighting at the coarse point (I, J, K) <- fine (2I+1, 2J+1, 2K+1) in
 // 0-based indices, weights (1/4, 1/2, 1/4) per axis, summed z, y, x in order.
 template <typename T>
 __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rr, T* __restrict__ bc,
-                           const int* active) {
+                           const Coef<T>* cc, const int* active) {
   PointIdx p;
   if (!point_index(gc, p)) return;
   if (active && !active[p.b]) return;
@@ -78,7 +78,7 @@ __global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rr, T* __rest
 #pragma unroll
       for (int a = -1; a <= 1; ++a) s = fma(wcb * w[a + 1], ldg(row + a), s);
     }
-  bc[p.b * gc.fs + p.idx] = s;
+  bc[p.b * gc.fs + p.idx] = s * cc[p.b].rs;
 }
 
 // Trilinear prolongation, one thread per coarse cell.  In 1-based indices the
@@ -104,7 +104,7 @@ __device__ __forceinline__ T cval(const T* __restrict__ e, const Grid& gc, int i
 
 template <typename T>
 __global__ void k_prolong_add(Grid gc, Grid gf, const T* __restrict__ ec, long long ecs,
-                              T* __restrict__ uf, long long ufs, const int* active) {
+                              const T* src, T* uf, long long ufs, const int* active) {
   using V2 = typename Vec2<T>::type;
   const int nc1 = gc.N + 1;  // cells per axis
   const int cx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -142,6 +142,22 @@ __global__ void k_prolong_add(Grid gc, Grid gf, const T* __restrict__ ec, long l
   const int Nf = gf.N;
   const int fx = 2 * cx, fy0 = 2 * cy, fz0 = 2 * cz;  // 0-based fine index of the mid points
   T* u = uf + b * ufs;
+  const T* us = src + b * ufs;
+  // src may be uf: every value is loaded before the first store, so that the
+  // loads need not wait for stores they might alias (each point is read and
+  // written by this thread only)
+  V2 o[2][2];
+  T o1[2][2];
+#pragma unroll
+  for (int mz = 0; mz < 2; ++mz)
+#pragma unroll
+    for (int my = 0; my < 2; ++my) {
+      const int fz = fz0 + mz, fy = fy0 + my;
+      if (fz >= Nf || fy >= Nf) continue;
+      const T* srow = us + (long long)fz * gf.plane + (long long)fy * gf.px;
+      if (fx + 1 < Nf) o[mz][my] = *reinterpret_cast<const V2*>(srow + fx);
+      else if (fx < Nf) o1[mz][my] = srow[fx];
+    }
 #pragma unroll
   for (int mz = 0; mz < 2; ++mz) {
     const int fz = fz0 + mz;
@@ -159,12 +175,12 @@ __global__ void k_prolong_add(Grid gc, Grid gf, const T* __restrict__ ec, long l
       }
       T* row = u + (long long)fz * gf.plane + (long long)fy * gf.px;
       if (fx + 1 < Nf) {
-        V2 o = *reinterpret_cast<V2*>(row + fx);
-        o.x += val[0];
-        o.y += val[1];
-        *reinterpret_cast<V2*>(row + fx) = o;
+        V2 r = o[mz][my];
+        r.x += val[0];
+        r.y += val[1];
+        *reinterpret_cast<V2*>(row + fx) = r;
       } else if (fx < Nf) {
-        row[fx] += val[0];
+        row[fx] = o1[mz][my] + val[0];
       }
     }
   }
@@ -398,32 +414,31 @@ __global__ void k_copy(Grid g, const double* __restrict__ s, long long ss, doubl
 // ---------------------------------------------------------------------------
 
 template <typename T>
-cudaError_t launch_jacobi_zero(const Grid& g, int B, const T* r, T* e, const Coef<T>* coef,
-                               bool exact, const int* active, cudaStream_t st) {
+cudaError_t launch_solve_one(const Grid& g, int B, const T* r, T* e, const Coef<T>* coef,
+                             const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  k_jacobi_zero<T><<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, r, e, coef, exact ? 1 : 0,
-                                                              active);
+  k_solve_one<T><<<point_grid(g, B), dim3(32, 8), 0, st>>>(g, r, e, coef, active);
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, int B, const T* rr, T* bc,
-                            const int* active, cudaStream_t st) {
+                            const Coef<T>* cc, const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  k_restrict<T><<<point_grid(gc, B), dim3(32, 8), 0, st>>>(gf, gc, rr, bc, active);
+  k_restrict<T><<<point_grid(gc, B), dim3(32, 8), 0, st>>>(gf, gc, rr, bc, cc, active);
   count_launch();
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_add(const Grid& gc, const Grid& gf, int B, const T* ec,
-                               long long ec_stride, T* uf, long long uf_stride,
+                               long long ec_stride, const T* src, T* uf, long long uf_stride,
                                const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
   const int nc1 = gc.N + 1;
   k_prolong_add<T><<<dim3((nc1 + 31) / 32, (nc1 + 7) / 8, nc1 * B), dim3(32, 8), 0, st>>>(
-      gc, gf, ec, ec_stride, uf, uf_stride, active);
+      gc, gf, ec, ec_stride, src, uf, uf_stride, active);
   count_launch();
   return cudaGetLastError();
 }
@@ -531,12 +546,12 @@ cudaError_t launch_copy(const Grid& g, int B, const double* src, long long src_s
 }
 
 #define H3D_INST(T)                                                                            \
-  template cudaError_t launch_jacobi_zero<T>(const Grid&, int, const T*, T*, const Coef<T>*,   \
-                                             bool, const int*, cudaStream_t);                   \
+  template cudaError_t launch_solve_one<T>(const Grid&, int, const T*, T*, const Coef<T>*,     \
+                                           const int*, cudaStream_t);                           \
   template cudaError_t launch_restrict<T>(const Grid&, const Grid&, int, const T*, T*,         \
-                                          const int*, cudaStream_t);                            \
+                                          const Coef<T>*, const int*, cudaStream_t);            \
   template cudaError_t launch_prolong_add<T>(const Grid&, const Grid&, int, const T*, long long,\
-                                             T*, long long, const int*, cudaStream_t);          \
+                                             const T*, T*, long long, const int*, cudaStream_t);\
   template cudaError_t launch_update<T>(const Grid&, int, const T*, double*, long long,        \
                                         const int*, cudaStream_t);
 H3D_INST(double)

@@ -15,10 +15,12 @@
 //    library keeps it until the process exits.
 //  - The first call on a device, with that device current, looks the array's
 //    device address up with cudaGetSymbolAddress (host code cannot use the
-//    array's name as a device pointer) and builds the host-side solver state;
-//    make that first call before any stream capture.
+//    array's name as a device pointer) and builds the host-side solver state.
 //  - Every call is synchronous: it waits for its stream to finish before it
-//    returns (host buffers are read and written on that stream).
+//    returns (host buffers are read and written on that stream), so no call
+//    can be part of a CUDA graph: a call made while its stream is being
+//    captured returns HEAT3D_EINVAL before it touches the stream, and the
+//    capture stays valid.
 //  - All calls on a device share the array and it keeps the last call's
 //    contents; the solver clears what must start at zero (the residual norms
 //    each solve, the whole array when the grid, stencil or precision changes).
@@ -67,6 +69,11 @@ int mg_vcycle_noalloc(int N, int order, int precision, double c, const double* r
   if ((order != 2 && order != 4) || (precision != HEAT3D_FP64 && precision != HEAT3D_MIXED) ||
       !rhs || !u || max_cycles < 0 || !(c >= 0))
     return fail(HEAT3D_EINVAL, "bad arguments");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess ||
+      cap != cudaStreamCaptureStatusNone)
+    return fail(HEAT3D_EINVAL,
+                "mg_vcycle_noalloc is synchronous and cannot run while its stream is captured");
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return fail(HEAT3D_ECUDA, "no current CUDA device");

@@ -6,8 +6,9 @@
 // launch and tail latency set the solve time.  Here one cooperative launch
 // runs the solve from the first FP64 residual to the last stop check:
 //  * the levels with N >= 15 run grid-wide, each operation (Jacobi sweep,
-//    residual, restriction with the next level's zero-guess sweep,
-//    prolongation, the FP64 residual and its norm) followed by a grid barrier;
+//    residual, restriction into the next level's scaled right-hand side,
+//    which is also its first iterate, prolongation, the FP64 residual and its
+//    norm) followed by a grid barrier;
 //    a block takes chunks of 256 consecutive points of one item;
 //  * the levels with N <= 7 run in one block per item, in shared memory
 //    (vcycle_small_body, the code of the fused coarse kernel);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
   for (int b = threadIdx.x; b < B; b += blockDim.x) act[b] = __ldcg(a.active + b);
   __syncthreads();
 
-  // r = b - A u in FP64 (stored as T), e0 = wd r, max |r| per item into slot
+  // r = b - A u in FP64, b' = wd (T) r, max |r| per item into slot
   auto resid64 = [&](int slot) {
     const Grid& g = a.g[0];
     for_points_max(g.N, B, act, red, a.norm2 + (size_t)slot * B,
@@ -206,13 +207,12 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
                      const Coef<double> c = a.c64[b];
                      const double res = a_res<double, ORDER>(c.d, c.e, c.e2, __ldcg(ub + idx), s1,
                                                              s2, __ldcg(a.rhs + b * a.bs + idx));
-                     const T rt = (T)res;
-                     a.b[0][b * g.fs + idx] = rt;
-                     a.e[0][b * g.fs + idx] = a.cf[0][b].wd * rt;
+                     a.b[0][b * g.fs + idx] = a.cf[0][b].wd * (T)res;
                      return abs_bits(res);
                    });
   };
-  // damped Jacobi on level k: dst = src + wd (b - A src), or u += that (upd)
+  // damped Jacobi on level k: dst = src + wd (b - A src) = al src + be S + b',
+  // or u += that (upd)
   auto jacobi = [&](int k, const T* src, T* dst, bool upd) {
     const Grid& g = a.g[k];
     for_points(g.N, B, act, [&](int b, int i, int j, int kk) {
@@ -221,9 +221,8 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
       T s1, s2;
       nsums_c<T, ORDER>(f, g, i, j, kk, s1, s2);
       const Coef<T> c = a.cf[k][b];
-      const T cc = __ldcg(f + idx);
-      const T res = a_res<T, ORDER>(c.d, c.e, c.e2, cc, s1, s2, __ldcg(a.b[k] + b * g.fs + idx));
-      const T v = fma(c.wd, res, cc);
+      const T v = jacobi_point<T, ORDER>(c.al, c.be, c.be2, __ldcg(f + idx), s1, s2,
+                                         __ldcg(a.b[k] + b * g.fs + idx));
       if (upd) {
         double* up = a.u + b * a.us + idx;
         *up = __ldcg(up) + (double)v;
@@ -232,7 +231,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
       }
     });
   };
-  // dst = b - A src on level k
+  // dst = t' = wd (b - A src) = b' - om src + be S on level k
   auto resid = [&](int k, const T* src, T* dst) {
     const Grid& g = a.g[k];
     for_points(g.N, B, act, [&](int b, int i, int j, int kk) {
@@ -241,13 +240,12 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
       T s1, s2;
       nsums_c<T, ORDER>(f, g, i, j, kk, s1, s2);
       const Coef<T> c = a.cf[k][b];
-      dst[b * g.fs + idx] =
-          a_res<T, ORDER>(c.d, c.e, c.e2, __ldcg(f + idx), s1, s2, __ldcg(a.b[k] + b * g.fs + idx));
+      dst[b * g.fs + idx] = resid_point<T, ORDER>(c.om, c.be, c.be2, __ldcg(f + idx), s1, s2,
+                                                  __ldcg(a.b[k] + b * g.fs + idx));
     });
   };
-  // full weighting of rr (level k) into b of level k+1; with jz also the
-  // zero-guess Jacobi sweep e = wd b of level k+1
-  auto restrict_to = [&](int k, const T* rr, bool jz) {
+  // full weighting of rr (level k) into b' of level k+1 (times rs)
+  auto restrict_to = [&](int k, const T* rr) {
     const Grid& gf = a.g[k];
     const Grid& gc = a.g[k + 1];
     for_points(gc.N, B, act, [&](int b, int i, int j, int kk) {
@@ -265,12 +263,12 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
           for (int cx = -1; cx <= 1; ++cx) s = fma(wcb * w[cx + 1], __ldcg(row + cx), s);
         }
       const long long o = b * gc.fs + (long long)kk * gc.plane + (long long)j * gc.px + i;
-      a.b[k + 1][o] = s;
-      if (jz) a.e[k + 1][o] = a.cf[k + 1][b].wd * s;
+      a.b[k + 1][o] = s * a.cf[k + 1][b].rs;
     });
   };
-  // uf (level k) += trilinear prolongation of ec (level k+1), one coarse cell per thread
-  auto prolong = [&](int k, const T* ec, T* uf) {
+  // uf (level k) = src + trilinear prolongation of ec (level k+1), one coarse
+  // cell per thread (src may be uf)
+  auto prolong = [&](int k, const T* ec, const T* src, T* uf) {
     const Grid& gf = a.g[k];
     const Grid& gc = a.g[k + 1];
     const int Nc = gc.N, Nf = gf.N;
@@ -304,6 +302,20 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
           Y[z][1][mx] = X[z][1][mx];
         }
       T* u = uf + b * gf.fs;
+      const T* us = src + b * gf.fs;
+      // all loads before the first store (src may be uf; each point is read
+      // and written by this thread only)
+      T o[2][2][2];
+#pragma unroll
+      for (int mz = 0; mz < 2; ++mz)
+#pragma unroll
+        for (int my = 0; my < 2; ++my)
+#pragma unroll
+          for (int mx = 0; mx < 2; ++mx) {
+            const int fz = 2 * cz + mz, fy = 2 * cy + my, fx = 2 * cx + mx;
+            if (fz < Nf && fy < Nf && fx < Nf)
+              o[mz][my][mx] = __ldcg(us + (long long)fz * gf.plane + (long long)fy * gf.px + fx);
+          }
 #pragma unroll
       for (int mz = 0; mz < 2; ++mz) {
         const int fz = 2 * cz + mz;
@@ -319,8 +331,7 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
             const T wv = mz == 0 ? Y[0][my][mx] + Y[1][my][mx] : Y[1][my][mx];
             const int na = (mx == 0) + (my == 0) + (mz == 0);
             const T val = na == 0 ? wv : wv * (na == 1 ? T(0.5) : na == 2 ? T(0.25) : T(0.125));
-            T* o = u + (long long)fz * gf.plane + (long long)fy * gf.px + fx;
-            *o = __ldcg(o) + val;
+            u[(long long)fz * gf.plane + (long long)fy * gf.px + fx] = o[mz][my][mx] + val;
           }
         }
       }
@@ -372,8 +383,9 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
     T* cur[kMaxLevels];
     T* oth[kMaxLevels];
     for (int k = 0; k < A.kb; ++k) {
-      T* c = a.e[k];
-      T* o = a.t[k];
+      // b' (a.b[k]) is the first iterate and is never written in the cycle
+      T* c = a.b[k];
+      T* o = a.e[k];
       int first = 1;
       if (k == 0 && warm) {
         c = res0;
@@ -383,11 +395,16 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
       for (int s = first; s < a.nu1; ++s) {
         jacobi(k, c, o, false);
         if (!grid_barrier(ctl, gen)) return false;
-        T* tmp = c; c = o; o = tmp;
+        if (c == a.b[k]) {
+          c = o;
+          o = o == a.e[k] ? a.t[k] : a.e[k];
+        } else {
+          T* tmp = c; c = o; o = tmp;
+        }
       }
       resid(k, c, o);
       if (!grid_barrier(ctl, gen)) return false;
-      restrict_to(k, o, k + 1 < A.kb);
+      restrict_to(k, o);
       if (!grid_barrier(ctl, gen)) return false;
       cur[k] = c;
       oth[k] = o;
@@ -398,8 +415,13 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
       const T* ce = k + 1 == A.kb ? a.e[A.kb] : cur[k + 1];
       T* c = cur[k];
       T* o = oth[k];
-      prolong(k, ce, c);
+      T* dst = c == a.b[k] ? o : c;
+      prolong(k, ce, c, dst);
       if (!grid_barrier(ctl, gen)) return false;
+      if (c == a.b[k]) {
+        c = dst;
+        o = dst == a.e[k] ? a.t[k] : a.e[k];
+      }
       bool added = false;
       for (int s = 0; s < a.nu2; ++s) {
         const bool upd = k == 0 && final && s == a.nu2 - 1;

@@ -382,6 +382,7 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
     for (int b = 0; b < B; ++b) {
       const double cc = cvals[b];
       Coef<double> q;
+      double omega;
       q.e2 = 0.0;
       if (order == kCompact) {
         // W - c L: centre 1/2 + 4c/h^2, faces 1/12 - c/(3h^2), edges -c/(6h^2);
@@ -389,19 +390,27 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
         q.e = cc / (3.0 * h * h) - 1.0 / 12.0;
         q.e2 = cc / (6.0 * h * h);
         q.d = 0.5 + 4.0 * cc / (h * h);
-        q.wd = (12.0 / 11.0) / q.d;
+        omega = 12.0 / 11.0;
         q.a11 = q.d;
       } else if (order == 2) {
         q.e = cc / (h * h);
         q.d = 1.0 + 6.0 * q.e;
-        q.wd = (6.0 / 7.0) / q.d;
+        omega = 6.0 / 7.0;
         q.a11 = 1.0 + 6.0 * q.e;
       } else {
         q.e = cc / (12.0 * h * h);
         q.d = 1.0 + 90.0 * q.e;
-        q.wd = (9.0 / 11.0) / q.d;
+        omega = 9.0 / 11.0;
         q.a11 = 1.0 + 84.0 * q.e;
       }
+      // the scaled V-cycle's coefficients (common.cuh): v = al u + be S + b'
+      q.wd = omega / q.d;
+      q.al = 1.0 - omega;
+      q.om = omega;
+      q.be = q.wd * q.e;
+      q.be2 = q.wd * q.e2;
+      q.a11w = q.wd * q.a11;
+      q.rs = k > 0 ? q.wd / cd[(size_t)(k - 1) * B + b].wd : 1.0;
       cd[(size_t)k * B + b] = q;
       if (k == 0) c64[b] = q;
     }
@@ -414,7 +423,9 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
       std::vector<Coef<float>> cf(B);
       for (int b = 0; b < B; ++b) {
         const Coef<double>& q = cd[(size_t)k * B + b];
-        cf[b] = Coef<float>{(float)q.d, (float)q.e, (float)q.wd, (float)q.a11, (float)q.e2};
+        cf[b] = Coef<float>{(float)q.d,  (float)q.e,  (float)q.wd,  (float)q.a11,
+                            (float)q.e2, (float)q.al, (float)q.om,  (float)q.be,
+                            (float)q.be2, (float)q.rs, (float)q.a11w};
       }
       CK(cudaMemcpyAsync((Coef<float>*)L.coefT + base, cf.data(), sizeof(Coef<float>) * B,
                          cudaMemcpyHostToDevice, c->st));
@@ -468,9 +479,12 @@ static const Coef<T>* coefT(SdcLevel& L, int slot, int k, int b0) {
   return (const Coef<T>*)L.coefT + ((size_t)slot * L.nmg + k) * L.B + b0;
 }
 
-// One V(nu1, nu2) cycle on level k for the error equation A e = b_k.  On the
-// finest level the first smoothing result e_0 = wd * r was written by the
-// residual kernel and the last post-smoothing sweep adds its result to u64.
+// One V(nu1, nu2) cycle on level k for the error equation A e = b_k, every
+// level holding its scaled right-hand side b' = wd b (slot 0; see Coef): on
+// the finest level the FP64 residual kernel wrote it, on the others the
+// restriction.  b' is also the first Jacobi iterate (the sweep from zero) and
+// is never written during the cycle; the iterates alternate between slots 1
+// and 2.  On level 0 the last post-smoothing sweep adds its result to u64.
 // Returns the buffer holding the level's correction (nullptr on level 0).
 // Algorithmic cost per point of one damped-Jacobi sweep (bytes, FP64 pipe
 // operations, flops); `upd` adds the result to the FP64 solution.
@@ -478,8 +492,8 @@ template <typename T>
 static void jacobi_cost(int order, bool upd, double* bytes, double* dp, double* fl) {
   const double ts = sizeof(T);
   // neighbour sums + fused multiply-adds (an FMA counts 2 flops)
-  const double ops = order == 2 ? 8.0 : order == 4 ? 14.0 : 20.0;
-  const double flops = order == 2 ? 11.0 : order == 4 ? 18.0 : 24.0;
+  const double ops = order == 2 ? 7.0 : order == 4 ? 13.0 : 19.0;
+  const double flops = order == 2 ? 9.0 : order == 4 ? 16.0 : 22.0;
   *bytes = upd ? 2.0 * ts + 16.0 : 3.0 * ts;
   *dp = (sizeof(T) == 8 ? ops : 0.0) + (upd ? 1.0 : 0.0);
   *fl = flops + (upd ? 1.0 : 0.0);
@@ -490,14 +504,14 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
                         const int* act, double* u64, long long us, T** result, bool warm = false,
                         bool final = true) {
   // Level 0 options: `warm` starts from the correction in *result (else from
-  // e_0 = wd r written by the residual kernel); `final` adds the correction to
-  // u64 in the last post-smoothing sweep (else *result returns its buffer).
+  // b' itself); `final` adds the correction to u64 in the last post-smoothing
+  // sweep (else *result returns its buffer).
   const bool prof_here = k == 0 && &L == &c->lv[0];
   const Grid& g = L.mg[k];
   const int order = L.L.order;
   const int nu1 = c->cfg.mg.nu1, nu2 = c->cfg.mg.nu2;
   cudaStream_t st = c->st;
-  T* b = mgbuf<T>(L, k, 0, b0);
+  T* bp = mgbuf<T>(L, k, 0, b0);
   T* e = mgbuf<T>(L, k, 1, b0);
   T* t = mgbuf<T>(L, k, 2, b0);
   const Coef<T>* cf = coefT<T>(L, slot, k, b0);
@@ -512,13 +526,13 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
       Ns[l] = L.mg[k + l].N;
       cfs[l] = coefT<T>(L, slot, k + l, b0);
     }
-    CK(launch_vcycle_small<T>(order, nl, Ns, cfs, B, b, e, g, nu1, nu2, act, st));
+    CK(launch_vcycle_small<T>(order, nl, Ns, cfs, B, bp, e, g, nu1, nu2, act, st));
     c->bytes += 2.0 * ts * pts;
     *result = e;
     return HEAT3D_OK;
   }
   if (g.N == 1) {
-    CK(launch_jacobi_zero<T>(g, B, b, e, cf, true, act, st));
+    CK(launch_solve_one<T>(g, B, bp, e, cf, act, st));
     if (k == 0 && final) {
       CK(launch_update<T>(g, B, e, u64, us, act, st));
       *result = nullptr;
@@ -527,18 +541,23 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
     }
     return HEAT3D_OK;
   }
-  if (k > 0) {
-    CK(launch_jacobi_zero<T>(g, B, b, e, cf, false, act, st));
-    c->bytes += 2.0 * ts * pts;
-  }
-  T* cur = e;
-  T* oth = t;
+  T* cur = bp;
+  T* oth = e;
   int first = 1;
   if (k == 0 && warm) {
     cur = *result;
     oth = cur == e ? t : e;
     first = 0;
   }
+  // after a sweep cur -> oth: the iterates then alternate between e and t
+  auto advance = [&]() {
+    if (cur == bp) {
+      cur = oth;
+      oth = oth == e ? t : e;
+    } else {
+      std::swap(cur, oth);
+    }
+  };
   // profiled fine-level Jacobi launches: all of them, or those that store the
   // error without the FP64 update
   auto prof_jacobi = [&](bool upd) {
@@ -548,27 +567,35 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   };
   for (int s = first; s < nu1; ++s) {
     int pr = prof_jacobi(false);
-    CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
+    CK(launch_jacobi<T>(order, g, B, cur, bp, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
       jacobi_cost<T>(order, false, &cb, &cd, &cfl);
       h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
     }
     c->bytes += 3.0 * ts * pts;
-    std::swap(cur, oth);
+    advance();
   }
-  CK(launch_resid<T>(order, g, B, cur, b, oth, cf, act, L.shapeT[k], st));
-  CK(launch_restrict<T>(g, L.mg[k + 1], B, oth, mgbuf<T>(L, k + 1, 0, b0), act, st));
+  CK(launch_resid<T>(order, g, B, cur, bp, oth, cf, act, L.shapeT[k], st));
+  CK(launch_restrict<T>(g, L.mg[k + 1], B, oth, mgbuf<T>(L, k + 1, 0, b0),
+                        coefT<T>(L, slot, k + 1, b0), act, st));
   c->bytes += 3.0 * ts * pts + ts * pts * (1.0 + 1.0 / 8.0);
   T* ce = nullptr;
   RET(vcycle_level<T>(c, L, slot, k + 1, b0, B, act, u64, us, &ce));
-  CK(launch_prolong_add<T>(L.mg[k + 1], g, B, ce, L.mg[k + 1].fs, cur, g.fs, act, st));
+  // prolongation into the iterate, or (no pre-smoothing sweep ran) from b'
+  // into the free buffer that held the restricted residual
+  T* dst = cur == bp ? oth : cur;
+  CK(launch_prolong_add<T>(L.mg[k + 1], g, B, ce, L.mg[k + 1].fs, cur, dst, g.fs, act, st));
   c->bytes += ts * pts * (2.0 + 1.0 / 8.0);
+  if (cur == bp) {
+    cur = dst;
+    oth = dst == e ? t : e;
+  }
   for (int s = 0; s < nu2; ++s) {
     const bool upd = k == 0 && final && s == nu2 - 1;
     int pr = prof_jacobi(upd);
-    if (upd) CK(launch_jacobi<T>(order, g, B, cur, b, nullptr, u64, us, cf, act, L.shapeT[k], st));
-    else CK(launch_jacobi<T>(order, g, B, cur, b, oth, nullptr, 0, cf, act, L.shapeT[k], st));
+    if (upd) CK(launch_jacobi<T>(order, g, B, cur, bp, nullptr, u64, us, cf, act, L.shapeT[k], st));
+    else CK(launch_jacobi<T>(order, g, B, cur, bp, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
       jacobi_cost<T>(order, upd, &cb, &cd, &cfl);
@@ -736,7 +763,6 @@ static double persist_step_bytes(const SdcLevel& L, int inner, int nu1, int nu2)
     const bool warm = q > 0, final = q == inner - 1;
     for (int k = 0; k < kb; ++k) {
       const double n = (double)L.mg[k].N * L.mg[k].N * L.mg[k].N;
-      if (k > 0) by += 2.0 * ts * n;
       by += (k == 0 && warm ? nu1 : nu1 - 1) * 3.0 * ts * n;
       by += 3.0 * ts * n + ts * n * (1.0 + 1.0 / 8.0);
       by += ts * n * (2.0 + 1.0 / 8.0);
@@ -747,7 +773,7 @@ static double persist_step_bytes(const SdcLevel& L, int inner, int nu1, int nu2)
     by += 2.0 * ts * nb;
   }
   const double n0 = (double)L.mg[0].N * L.mg[0].N * L.mg[0].N;
-  return by + (16.0 + 2.0 * ts) * n0;
+  return by + (16.0 + ts) * n0;
 }
 
 template <typename T>
@@ -761,8 +787,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
   int* act = L.active + b0;
   std::vector<int> ha(B, 1);
   CK(cudaMemcpyAsync(act, ha.data(), sizeof(int) * B, cudaMemcpyHostToDevice, st));
-  T* r = mgbuf<T>(L, 0, 0, b0);
-  T* e0 = mgbuf<T>(L, 0, 1, b0);
+  T* bp = mgbuf<T>(L, 0, 0, b0);  // b' = wd r, written by the FP64 residual
   const Coef<T>* cf = coefT<T>(L, slot, 0, b0);
   const Coef<double>* c64 = L.coef64 + (size_t)slot * L.B + b0;
   const double pts = (double)g.N * g.N * g.N * B;
@@ -771,14 +796,14 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
   auto residual = [&]() -> int {
     CK(cudaMemsetAsync(L.norms + b0, 0, sizeof(unsigned long long) * B, st));
     int pr = lev == 0 ? h3d_prof_begin(c, HEAT3D_PROF_RESID64_FINE) : -1;
-    CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, r, e0, cf, L.norms + b0, act, L.shape64, st));
+    CK(launch_resid64<T>(order, g, B, u, us, rhs, bs, c64, bp, cf, L.norms + b0, act, L.shape64, st));
     if (pr >= 0) {
-      // neighbour sums + 2 FMAs (+ the FP64 e0 multiply when T is double)
+      // neighbour sums + 2 FMAs (+ the FP64 b' multiply when T is double)
       double dp = (order == 2 ? 7.0 : order == 4 ? 13.0 : 19.0) + (sizeof(T) == 8 ? 1.0 : 0.0);
       double fl = (order == 2 ? 9.0 : order == 4 ? 16.0 : 22.0) + 1.0;
-      h3d_prof_end(c, pr, (16.0 + 2.0 * sizeof(T)) * pts, dp * pts, fl * pts);
+      h3d_prof_end(c, pr, (16.0 + sizeof(T)) * pts, dp * pts, fl * pts);
     }
-    c->bytes += (16.0 + 2.0 * sizeof(T)) * pts;
+    c->bytes += (16.0 + sizeof(T)) * pts;
     return HEAT3D_OK;
   };
   // inner = 0 (mixed precision, tolerance solves): the number of FP32
@@ -834,7 +859,7 @@ static int mg_solve_T(heat3d_ctx* c, int lev, int slot, int b0, int B, double* u
     long long done = 0;
     for (int b = 0; b < B; ++b) done += hcyc[b];
     c->bytes += (double)done * persist_step_bytes<T>(L, inner, c->cfg.mg.nu1, c->cfg.mg.nu2) +
-                (16.0 + 2.0 * sizeof(T)) * pts;
+                (16.0 + sizeof(T)) * pts;
     return solve_outcome(c, lev, B, inner, fixed, tol, max_cycles, tl, hcyc, last, hnan, s);
   }
   int nin = inner;  // V-cycles of the next refinement step
@@ -1183,7 +1208,8 @@ int h3d_fas_interpolate(heat3d_ctx* c, int b0, int B) {
       CK(launch_prolong_add_mid(npts, G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, st));
     }
   } else {
-    CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
+    CK(launch_prolong_add<double>(G.g, F.g, B * MF, D, gf, F.U + (size_t)b0 * MF * ff,
+                                  F.U + (size_t)b0 * MF * ff, ff, nullptr, st));
   }
   RET(h3d_eval_F(c, 0, b0, B));
   const double pf = (double)F.L.N * F.L.N * F.L.N * B;

@@ -37,7 +37,7 @@ cudaError_t launch_lap(int order, const Grid& g, int B, const double* u, long lo
 
 #define H3D_INST(T)                                                                            \
   template cudaError_t launch_resid64<T>(int, const Grid&, int, const double*, long long,      \
-                                         const double*, long long, const Coef<double>*, T*, T*, \
+                                         const double*, long long, const Coef<double>*, T*,     \
                                          const Coef<T>*, unsigned long long*, const int*, Shape, \
                                          cudaStream_t);                                         \
   template cudaError_t launch_jacobi<T>(int, const Grid&, int, const T*, const T*, T*, double*, \

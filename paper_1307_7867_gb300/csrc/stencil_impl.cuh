@@ -229,7 +229,9 @@ struct OpLap {
   }
 };
 
-// r = b - A u in FP64, stored as TR; e0 = wd r (first Jacobi iterate from zero).
+// r = b - A u in FP64 (its max |.| is the stop rule's norm), stored as the
+// scaled right-hand side of the error equation b' = wd (TR) r, which is also
+// the first Jacobi iterate from zero.
 template <int ORDER, typename TR>
 struct OpResid64 {
   using T = double;
@@ -237,36 +239,48 @@ struct OpResid64 {
   const double* u; long long us;
   const double* bb; long long bs;
   const Coef<double>* coef;
-  TR* r; TR* e0; const Coef<TR>* coef_r; long long rs;
+  TR* bp; const Coef<TR>* coef_r; long long rs;
   double d, e; TR wd;
   const double* b_;
-  TR* r_;
-  TR* e0_;
+  TR* bp_;
   double e2;
   __device__ const double* src(int b) const { return u + b * us; }
   __device__ void init(int b) {
     d = coef[b].d;
     e = coef[b].e;
     e2 = coef[b].e2;
-    wd = e0 ? coef_r[b].wd : TR(0);
+    wd = coef_r[b].wd;
     b_ = bb + b * bs;
-    r_ = r + b * rs;
-    e0_ = e0 ? e0 + b * rs : nullptr;
+    bp_ = bp + b * rs;
   }
   __device__ Ex load(int idx) const { return Ex{b_[idx]}; }
   __device__ double apply(int idx, double c, double s1, double s2, const Ex& ex) {
     double res = a_res<double, ORDER>(d, e, e2, c, s1, s2, ex.b);
-    TR rt = (TR)res;
-    r_[idx] = rt;
-    if (e0_) e0_[idx] = wd * rt;
+    bp_[idx] = wd * (TR)res;
     return res;
   }
 };
 
-// Damped Jacobi on the error equation: v = e + wd (r - A e); stored (UPD =
-// false) or added to the FP64 solution u64 (UPD = true).  UPD is a template
-// parameter so that the stored variant contains no FP64 instruction at all
-// (a runtime branch is if-converted and would run the FP64 add everywhere).
+// One damped-Jacobi sweep on the error equation with the scaled right-hand
+// side r = b' = wd b: v = e + wd (b - A e) = al e + be S + b' (compact:
+// + be2 S2), one multiply-add fewer than forming the residual first; stored
+// (UPD = false) or added to the FP64 solution u64 (UPD = true).  UPD is a
+// template parameter so that the stored variant contains no FP64 instruction
+// at all (a runtime branch is if-converted and would run the FP64 add
+// everywhere).
+template <typename T, int ORDER>
+__device__ __forceinline__ T jacobi_point(T al, T be, T be2, T c, T s1, T s2, T bp) {
+  if (ORDER == kCompact) return fma(al, c, fma(be, s1, fma(be2, s2, bp)));
+  return fma(al, c, fma(be, combine<T, ORDER>(s1, s2), bp));
+}
+// t' = wd (b - A e) = b' - om e + be S (compact: + be2 S2), the residual the
+// restriction takes on the scaled levels.
+template <typename T, int ORDER>
+__device__ __forceinline__ T resid_point(T om, T be, T be2, T c, T s1, T s2, T bp) {
+  if (ORDER == kCompact) return fma(-om, c, fma(be, s1, fma(be2, s2, bp)));
+  return fma(-om, c, fma(be, combine<T, ORDER>(s1, s2), bp));
+}
+
 template <typename TT, int ORDER, bool UPD>
 struct OpJacobi {
   using T = TT;
@@ -274,19 +288,17 @@ struct OpJacobi {
   const T* e; const T* r; T* out; long long fs;
   double* u64; long long u64s;
   const Coef<T>* coef;
-  T d, ec, wd;
+  T al, be, be2;
   const T* r_;
   T* o_;
   double* u_;
-  T e2c;
   __device__ const T* src(int b) const { return e + b * fs; }
   __host__ __device__ const T* src_base() const { return e; }
   __host__ __device__ long long src_stride() const { return fs; }
   __device__ void init(int b) {
-    d = coef[b].d;
-    ec = coef[b].e;
-    wd = coef[b].wd;
-    e2c = coef[b].e2;
+    al = coef[b].al;
+    be = coef[b].be;
+    be2 = coef[b].be2;
     r_ = r + b * fs;
     if (UPD) u_ = u64 + b * u64s;
     else o_ = out + b * fs;
@@ -298,8 +310,7 @@ struct OpJacobi {
     return x;
   }
   __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
-    T res = a_res<T, ORDER>(d, ec, e2c, c, s1, s2, ex.r);
-    T v = fma(wd, res, c);
+    T v = jacobi_point<T, ORDER>(al, be, be2, c, s1, s2, ex.r);
     if (UPD) u_[idx] = ex.u + (double)v;
     else o_[idx] = v;
     return 0.0;
@@ -325,10 +336,7 @@ struct OpJacobi {
     const float rr[4] = {ex.r.x, ex.r.y, ex.r.z, ex.r.w};
     float v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float res = a_res<float, ORDER>(d, ec, e2c, c[q], s1[q], s2[q], rr[q]);
-      v[q] = fmaf(wd, res, c[q]);
-    }
+    for (int q = 0; q < 4; ++q) v[q] = jacobi_point<float, ORDER>(al, be, be2, c[q], s1[q], s2[q], rr[q]);
     if (UPD) {
       const double w[4] = {ex.u01.x + (double)v[0], ex.u01.y + (double)v[1],
                            ex.u23.x + (double)v[2], ex.u23.y + (double)v[3]};
@@ -350,30 +358,30 @@ struct OpJacobi {
   }
 };
 
-// rr = r - A e
+// rr = t' = wd (b - A e) from the scaled right-hand side r = b'
 template <typename TT, int ORDER>
 struct OpResid {
   using T = TT;
   struct Ex { T r; };
   const T* e; const T* r; T* rr; long long fs;
   const Coef<T>* coef;
-  T d, ec;
+  T om, be;
   const T* r_;
   T* o_;
-  T e2c;
+  T be2;
   __device__ const T* src(int b) const { return e + b * fs; }
   __host__ __device__ const T* src_base() const { return e; }
   __host__ __device__ long long src_stride() const { return fs; }
   __device__ void init(int b) {
-    d = coef[b].d;
-    ec = coef[b].e;
-    e2c = coef[b].e2;
+    om = coef[b].om;
+    be = coef[b].be;
+    be2 = coef[b].be2;
     r_ = r + b * fs;
     o_ = rr + b * fs;
   }
   __device__ Ex load(int idx) const { return Ex{r_[idx]}; }
   __device__ double apply(int idx, T c, T s1, T s2, const Ex& ex) {
-    o_[idx] = a_res<T, ORDER>(d, ec, e2c, c, s1, s2, ex.r);
+    o_[idx] = resid_point<T, ORDER>(om, be, be2, c, s1, s2, ex.r);
     return 0.0;
   }
   static constexpr bool kVec4 = sizeof(TT) == 4;
@@ -385,7 +393,7 @@ struct OpResid {
     const float rr[4] = {ex.r.x, ex.r.y, ex.r.z, ex.r.w};
     float v[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = a_res<float, ORDER>(d, ec, e2c, c[q], s1[q], s2[q], rr[q]);
+    for (int q = 0; q < 4; ++q) v[q] = resid_point<float, ORDER>(om, be, be2, c[q], s1[q], s2[q], rr[q]);
     if (n >= 4) {
       *reinterpret_cast<float4*>(o_ + idx) = make_float4(v[0], v[1], v[2], v[3]);
     } else {
@@ -1551,20 +1559,20 @@ cudaError_t run_stencil(const Grid& g, int B, const int* active, unsigned long l
 template <typename TR>
 cudaError_t launch_resid64(int order, const Grid& g, int B, const double* u, long long u_stride,
                            const double* b, long long b_stride, const Coef<double>* coef,
-                           TR* r_out, TR* e0_out, const Coef<TR>* coef_r,
+                           TR* bp_out, const Coef<TR>* coef_r,
                            unsigned long long* norm_bits, const int* active, Shape sh,
                            cudaStream_t st) {
   if (order == kCompact) {
-    OpResid64<kCompact, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+    OpResid64<kCompact, TR> op{u, u_stride, b, b_stride, coef, bp_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
     return norm_bits ? run_stencil<kCompact, true>(g, B, active, norm_bits, op, sh, st)
                      : run_stencil<kCompact, false>(g, B, active, nullptr, op, sh, st);
   }
   if (order == 2) {
-    OpResid64<2, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+    OpResid64<2, TR> op{u, u_stride, b, b_stride, coef, bp_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
     return norm_bits ? run_stencil<2, true>(g, B, active, norm_bits, op, sh, st)
                      : run_stencil<2, false>(g, B, active, nullptr, op, sh, st);
   }
-  OpResid64<4, TR> op{u, u_stride, b, b_stride, coef, r_out, e0_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
+  OpResid64<4, TR> op{u, u_stride, b, b_stride, coef, bp_out, coef_r, g.fs, 0.0, 0.0, TR(0)};
   return norm_bits ? run_stencil<4, true>(g, B, active, norm_bits, op, sh, st)
                    : run_stencil<4, false>(g, B, active, nullptr, op, sh, st);
 }

@@ -85,3 +85,30 @@ def test_noalloc_mixed_precision_and_switching(H):
         g = got.cpu().numpy()
         tol = 1e-11 if prec == H.FP64 else 1e-9
         assert np.abs(g - refs[prec]).max() <= tol * np.abs(refs[prec]).max(), prec
+
+
+def test_noalloc_refuses_stream_capture(H):
+    """The call is synchronous, so it cannot be captured into a CUDA graph: under
+    capture it returns EINVAL before touching the stream, the capture stays
+    valid, and the next call outside the capture solves as before."""
+    N, order, c = 15, 2, 0.01
+    b = torch.from_numpy(inputs.random_field(N, seed=21)).cuda()
+    u = torch.zeros_like(b)
+    x = torch.zeros(16, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    err = None
+    with torch.cuda.graph(g, stream=s):
+        x.add_(1.0)
+        try:
+            H.mg_vcycle_noalloc(N, order, H.FP64, c, b, u, 2, -1.0, stream=s)
+        except H.Heat3DError as e:
+            err = e
+    assert err is not None and err.code == H.EINVAL
+    assert "captured" in str(err)
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(x.sum()) == 16.0
+    rc, st = H.mg_vcycle_noalloc(N, order, H.FP64, c, b, u, 2, -1.0, stream=s)
+    assert rc == H.OK and st["vcycles"] == 2
