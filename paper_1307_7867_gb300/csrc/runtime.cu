@@ -487,14 +487,15 @@ static const Coef<T>* coefT(SdcLevel& L, int slot, int k, int b0) {
 // and 2.  On level 0 the last post-smoothing sweep adds its result to u64.
 // Returns the buffer holding the level's correction (nullptr on level 0).
 // Algorithmic cost per point of one damped-Jacobi sweep (bytes, FP64 pipe
-// operations, flops); `upd` adds the result to the FP64 solution.
+// operations, flops); `upd` adds the result to the FP64 solution; `same`: the
+// iterate is b' itself (the sweep after the one from zero), read once.
 template <typename T>
-static void jacobi_cost(int order, bool upd, double* bytes, double* dp, double* fl) {
+static void jacobi_cost(int order, bool upd, bool same, double* bytes, double* dp, double* fl) {
   const double ts = sizeof(T);
   // neighbour sums + fused multiply-adds (an FMA counts 2 flops)
   const double ops = order == 2 ? 7.0 : order == 4 ? 13.0 : 19.0;
   const double flops = order == 2 ? 9.0 : order == 4 ? 16.0 : 22.0;
-  *bytes = upd ? 2.0 * ts + 16.0 : 3.0 * ts;
+  *bytes = (upd ? ts + 16.0 : 2.0 * ts) + (same ? 0.0 : ts);
   *dp = (sizeof(T) == 8 ? ops : 0.0) + (upd ? 1.0 : 0.0);
   *fl = flops + (upd ? 1.0 : 0.0);
 }
@@ -568,12 +569,10 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
   for (int s = first; s < nu1; ++s) {
     int pr = prof_jacobi(false);
     CK(launch_jacobi<T>(order, g, B, cur, bp, oth, nullptr, 0, cf, act, L.shapeT[k], st));
-    if (pr >= 0) {
-      double cb, cd, cfl;
-      jacobi_cost<T>(order, false, &cb, &cd, &cfl);
-      h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
-    }
-    c->bytes += 3.0 * ts * pts;
+    double cb, cd, cfl;
+    jacobi_cost<T>(order, false, cur == bp, &cb, &cd, &cfl);
+    if (pr >= 0) h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
+    c->bytes += cb * pts;
     advance();
   }
   CK(launch_resid<T>(order, g, B, cur, bp, oth, cf, act, L.shapeT[k], st));
@@ -598,7 +597,7 @@ static int vcycle_level(heat3d_ctx* c, SdcLevel& L, int slot, int k, int b0, int
     else CK(launch_jacobi<T>(order, g, B, cur, bp, oth, nullptr, 0, cf, act, L.shapeT[k], st));
     if (pr >= 0) {
       double cb, cd, cfl;
-      jacobi_cost<T>(order, upd, &cb, &cd, &cfl);
+      jacobi_cost<T>(order, upd, false, &cb, &cd, &cfl);
       h3d_prof_end(c, pr, cb * pts, cd * pts, cfl * pts);
     }
     if (upd) {
@@ -763,7 +762,10 @@ static double persist_step_bytes(const SdcLevel& L, int inner, int nu1, int nu2)
     const bool warm = q > 0, final = q == inner - 1;
     for (int k = 0; k < kb; ++k) {
       const double n = (double)L.mg[k].N * L.mg[k].N * L.mg[k].N;
-      by += (k == 0 && warm ? nu1 : nu1 - 1) * 3.0 * ts * n;
+      // warm: nu1 sweeps; cold: nu1 - 1 launched sweeps, the first reading b'
+      // once as both iterate and right-hand side
+      by += (k == 0 && warm) ? nu1 * 3.0 * ts * n
+                             : (nu1 > 1 ? 2.0 * ts * n + (nu1 - 2) * 3.0 * ts * n : 0.0);
       by += 3.0 * ts * n + ts * n * (1.0 + 1.0 / 8.0);
       by += ts * n * (2.0 + 1.0 / 8.0);
       for (int s = 0; s < nu2; ++s) by += (k == 0 && final && s == nu2 - 1) ? (2.0 * ts + 16.0) * n : 3.0 * ts * n;
