@@ -136,21 +136,21 @@ __device__ __forceinline__ void vcycle_small_body(const SmallArgs<T>& a, int ite
       ot[q] = fma(-c.om, cu[q], fma(c.be, combine_s<T, ORDER>(s1, s2), lb[l][q]));
     }
     __syncthreads();
-    // full weighting into the next level's scaled right-hand side
+    // full weighting (fw3) into the next level's scaled right-hand side
     const int Nc = a.N[l + 1];
-    const T rs = a.cf[l + 1][item].rs;
-    const T w[3] = {T(0.25), T(0.5), T(0.25)};
+    const T sc = a.cf[l + 1][item].rs * T(0.015625);
     for (int q = tid; q < Nc * Nc * Nc; q += nt) {
       const int I = q % Nc, J = (q / Nc) % Nc, K = q / (Nc * Nc);
-      const int fi = 2 * I + 1, fj = 2 * J + 1, fk = 2 * K + 1;
-      T sacc = T(0);
-      for (int cz = -1; cz <= 1; ++cz)
-        for (int cy = -1; cy <= 1; ++cy) {
-          const T wcb = w[cz + 1] * w[cy + 1];
-          const T* row = ot + ((fk + cz) * N + (fj + cy)) * N + fi;
-          for (int cx = -1; cx <= 1; ++cx) sacc = fma(wcb * w[cx + 1], row[cx], sacc);
+      T y[3];
+      for (int cz = 0; cz < 3; ++cz) {
+        T x[3];
+        for (int cy = 0; cy < 3; ++cy) {
+          const T* row = ot + ((2 * K + cz) * N + (2 * J + cy)) * N + 2 * I;
+          x[cy] = fw3(row[0], row[1], row[2]);
         }
-      lb[l + 1][q] = sacc * rs;
+        y[cz] = fw3(x[0], x[1], x[2]);
+      }
+      lb[l + 1][q] = fw3(y[0], y[1], y[2]) * sc;
     }
     cur[l] = cu;
     oth[l] = ot;

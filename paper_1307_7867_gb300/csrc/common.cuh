@@ -53,6 +53,21 @@ struct Coef {
 // Order code of the compact 19-point (Mehrstellen) stencil.
 constexpr int kCompact = 19;
 
+// Full weighting (Sec. 1.2) of a fine field onto coarse point (I, J, K), the
+// fine points 2I..2I+2, 2J..2J+2, 2K..2K+2 (0-based) with weights (1, 2, 1)
+// per axis, formed separably -- along x per fine row, then y per fine plane,
+// then z -- and scaled by 1/64 at the end:
+//   X = fw3(t(2I), t(2I+1), t(2I+2)), Y = fw3(X(2J), X(2J+1), X(2J+2)),
+//   value = fw3(Y(2K), Y(2K+1), Y(2K+2)) * (rs / 64).
+// Every implementation (the z-marching restriction kernel, which reuses the
+// plane sums Y of the fine planes two coarse planes share, the persistent
+// solve kernel, the fused coarse levels) uses exactly these operations, so
+// they agree bit for bit.
+template <typename T>
+__host__ __device__ __forceinline__ T fw3(T a, T b, T c) {
+  return fma(T(2), b, a + c);
+}
+
 // Per item, per SDC level: step data of the sweep (Sec. 1.1).
 struct ItemSDC {
   double dtS[kMaxNodes - 1][kMaxNodes];  // dt * S[m][j]

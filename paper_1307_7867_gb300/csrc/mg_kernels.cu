@@ -4,6 +4,8 @@
 // and the dense <-> pitched copies.  One thread per grid point of one item;
 // blockIdx.z = item * N + plane.  (The stencil kernels are in
 // stencil_impl.cuh.)
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace h3d {
@@ -57,28 +59,40 @@ __global__ void k_solve_one(Grid g, const T* __restrict__ r, T* __restrict__ e,
   e[o] = r[o] / coef[p.b].a11w;
 }
 
-// Full weighting at the coarse point (I, J, K) <- fine (2I+1, 2J+1, 2K+1) in
-// 0-based indices, weights (1/4, 1/2, 1/4) per axis, summed z, y, x in order.
+// Full weighting (fw3 in common.cuh) into the coarse level's scaled
+// right-hand side.  A thread owns coarse column (I, J) and marches over a
+// chunk of kc coarse planes: the plane sum Y of fine plane 2K+2 closes coarse
+// plane K and opens K+1, so each coarse point costs two plane sums (8
+// operations each), the z combination and the scaling: 19 operations instead
+// of 27 (plus 8 per chunk for its first plane).
 template <typename T>
-__global__ void k_restrict(Grid gf, Grid gc, const T* __restrict__ rr, T* __restrict__ bc,
-                           const Coef<T>* cc, const int* active) {
-  PointIdx p;
-  if (!point_index(gc, p)) return;
-  if (active && !active[p.b]) return;
-  const T w[3] = {T(0.25), T(0.5), T(0.25)};
-  const T* f = rr + p.b * gf.fs;
-  const int fi = 2 * p.i + 1, fj = 2 * p.j + 1, fk = 2 * p.k + 1;
-  T s = T(0);
-#pragma unroll
-  for (int c = -1; c <= 1; ++c)
-#pragma unroll
-    for (int b = -1; b <= 1; ++b) {
-      const T* row = f + (long long)(fk + c) * gf.plane + (long long)(fj + b) * gf.px + fi;
-      T wcb = w[c + 1] * w[b + 1];
-#pragma unroll
-      for (int a = -1; a <= 1; ++a) s = fma(wcb * w[a + 1], ldg(row + a), s);
-    }
-  bc[p.b * gc.fs + p.idx] = s * cc[p.b].rs;
+__global__ void __launch_bounds__(256) k_restrict(Grid gf, Grid gc, const T* __restrict__ rr,
+                                                  T* __restrict__ bc, const Coef<T>* cc, int kc,
+                                                  const int* active) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int nkc = (gc.N + kc - 1) / kc;
+  const int b = blockIdx.z / nkc;
+  const int K0 = (blockIdx.z - b * nkc) * kc, K1 = min(gc.N, K0 + kc);
+  if (I >= gc.N || J >= gc.N) return;
+  if (active && !active[b]) return;
+  const T* f = rr + b * gf.fs + (long long)(2 * J) * gf.px + 2 * I;  // fine (2I, 2J, 0)
+  const long long px = gf.px;
+  auto plane_sum = [&](int p) {
+    const T* q = f + (long long)p * gf.plane;
+    const T x0 = fw3(ldg(q), ldg(q + 1), ldg(q + 2));
+    const T x1 = fw3(ldg(q + px), ldg(q + px + 1), ldg(q + px + 2));
+    const T x2 = fw3(ldg(q + 2 * px), ldg(q + 2 * px + 1), ldg(q + 2 * px + 2));
+    return fw3(x0, x1, x2);
+  };
+  const T sc = cc[b].rs * T(0.015625);
+  T* out = bc + b * gc.fs + (long long)J * gc.px + I;
+  T ylo = plane_sum(2 * K0);
+  for (int K = K0; K < K1; ++K) {
+    const T y1 = plane_sum(2 * K + 1), y2 = plane_sum(2 * K + 2);
+    out[(long long)K * gc.plane] = fw3(ylo, y1, y2) * sc;
+    ylo = y2;
+  }
 }
 
 // Trilinear prolongation, one thread per coarse cell.  In 1-based indices the
@@ -426,7 +440,14 @@ template <typename T>
 cudaError_t launch_restrict(const Grid& gf, const Grid& gc, int B, const T* rr, T* bc,
                             const Coef<T>* cc, const int* active, cudaStream_t st) {
   if (B <= 0) return cudaSuccess;
-  k_restrict<T><<<point_grid(gc, B), dim3(32, 8), 0, st>>>(gf, gc, rr, bc, cc, active);
+  // coarse planes per thread: in FP64 (bound by the FP64 pipe) long runs that
+  // share plane sums, where there are columns enough to fill the GPU; in FP32
+  // (bound by memory latency and bandwidth) one plane per thread, for the
+  // most loads in flight
+  const int kc = sizeof(T) == 8 ? std::max(1, std::min(8, gc.N / 16)) : 1;
+  const int nkc = (gc.N + kc - 1) / kc;
+  k_restrict<T><<<dim3((gc.N + 31) / 32, (gc.N + 7) / 8, nkc * B), dim3(32, 8), 0, st>>>(
+      gf, gc, rr, bc, cc, kc, active);
   count_launch();
   return cudaGetLastError();
 }

@@ -244,26 +244,25 @@ __global__ void __launch_bounds__(kPersistThreads) k_mg_persist(PersistArgs<T> A
                                                   __ldcg(a.b[k] + b * g.fs + idx));
     });
   };
-  // full weighting of rr (level k) into b' of level k+1 (times rs)
+  // full weighting of rr (level k) into b' of level k+1 (fw3, times rs / 64)
   auto restrict_to = [&](int k, const T* rr) {
     const Grid& gf = a.g[k];
     const Grid& gc = a.g[k + 1];
     for_points(gc.N, B, act, [&](int b, int i, int j, int kk) {
-      const T w[3] = {T(0.25), T(0.5), T(0.25)};
-      const T* f = rr + b * gf.fs;
-      const int fi = 2 * i + 1, fj = 2 * j + 1, fk = 2 * kk + 1;
-      T s = T(0);
+      const T* f = rr + b * gf.fs + (long long)(2 * kk) * gf.plane + (long long)(2 * j) * gf.px + 2 * i;
+      T y[3];
 #pragma unroll
-      for (int cz = -1; cz <= 1; ++cz)
+      for (int cz = 0; cz < 3; ++cz) {
+        T x[3];
 #pragma unroll
-        for (int cy = -1; cy <= 1; ++cy) {
-          const T* row = f + (long long)(fk + cz) * gf.plane + (long long)(fj + cy) * gf.px + fi;
-          const T wcb = w[cz + 1] * w[cy + 1];
-#pragma unroll
-          for (int cx = -1; cx <= 1; ++cx) s = fma(wcb * w[cx + 1], __ldcg(row + cx), s);
+        for (int cy = 0; cy < 3; ++cy) {
+          const T* row = f + (long long)cz * gf.plane + (long long)cy * gf.px;
+          x[cy] = fw3(__ldcg(row), __ldcg(row + 1), __ldcg(row + 2));
         }
+        y[cz] = fw3(x[0], x[1], x[2]);
+      }
       const long long o = b * gc.fs + (long long)kk * gc.plane + (long long)j * gc.px + i;
-      a.b[k + 1][o] = s * a.cf[k + 1][b].rs;
+      a.b[k + 1][o] = fw3(y[0], y[1], y[2]) * (a.cf[k + 1][b].rs * T(0.015625));
     });
   };
   // uf (level k) = src + trilinear prolongation of ec (level k+1), one coarse
