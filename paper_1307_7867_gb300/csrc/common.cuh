@@ -53,6 +53,43 @@ struct Coef {
 // Order code of the compact 19-point (Mehrstellen) stencil.
 constexpr int kCompact = 19;
 
+// Coefficients of A = W - c Delta_h on a multigrid level of spacing h for
+// stencil `order` (Sec. 1.2; see Coef), with the damped-Jacobi weights of
+// the scaled V-cycle; wd_finer: wd of the next finer level (0 on the finest,
+// rs = 1 there).
+inline Coef<double> mg_level_coef(int order, double c, double h, double wd_finer) {
+  Coef<double> q;
+  double omega;
+  q.e2 = 0.0;
+  if (order == kCompact) {
+    // W - c L: centre 1/2 + 4c/h^2, faces 1/12 - c/(3h^2), edges -c/(6h^2);
+    // omega = 12/11 from local Fourier analysis of the Mehrstellen operator
+    q.e = c / (3.0 * h * h) - 1.0 / 12.0;
+    q.e2 = c / (6.0 * h * h);
+    q.d = 0.5 + 4.0 * c / (h * h);
+    omega = 12.0 / 11.0;
+    q.a11 = q.d;
+  } else if (order == 2) {
+    q.e = c / (h * h);
+    q.d = 1.0 + 6.0 * q.e;
+    omega = 6.0 / 7.0;
+    q.a11 = 1.0 + 6.0 * q.e;
+  } else {
+    q.e = c / (12.0 * h * h);
+    q.d = 1.0 + 90.0 * q.e;
+    omega = 9.0 / 11.0;
+    q.a11 = 1.0 + 84.0 * q.e;
+  }
+  q.wd = omega / q.d;
+  q.al = 1.0 - omega;
+  q.om = omega;
+  q.be = q.wd * q.e;
+  q.be2 = q.wd * q.e2;
+  q.a11w = q.wd * q.a11;
+  q.rs = wd_finer > 0.0 ? q.wd / wd_finer : 1.0;
+  return q;
+}
+
 // Full weighting (Sec. 1.2) of a fine field onto coarse point (I, J, K), the
 // fine points 2I..2I+2, 2J..2J+2, 2K..2K+2 (0-based) with weights (1, 2, 1)
 // per axis, formed separably -- along x per fine row, then y per fine plane,

@@ -380,37 +380,8 @@ int h3d_set_coefs(heat3d_ctx* c, int lev, int slot, int b0, int B, const double*
   for (int k = 0; k < L.nmg; ++k) {
     const double h = L.h[k];
     for (int b = 0; b < B; ++b) {
-      const double cc = cvals[b];
-      Coef<double> q;
-      double omega;
-      q.e2 = 0.0;
-      if (order == kCompact) {
-        // W - c L: centre 1/2 + 4c/h^2, faces 1/12 - c/(3h^2), edges -c/(6h^2);
-        // omega = 12/11 from local Fourier analysis of the Mehrstellen operator
-        q.e = cc / (3.0 * h * h) - 1.0 / 12.0;
-        q.e2 = cc / (6.0 * h * h);
-        q.d = 0.5 + 4.0 * cc / (h * h);
-        omega = 12.0 / 11.0;
-        q.a11 = q.d;
-      } else if (order == 2) {
-        q.e = cc / (h * h);
-        q.d = 1.0 + 6.0 * q.e;
-        omega = 6.0 / 7.0;
-        q.a11 = 1.0 + 6.0 * q.e;
-      } else {
-        q.e = cc / (12.0 * h * h);
-        q.d = 1.0 + 90.0 * q.e;
-        omega = 9.0 / 11.0;
-        q.a11 = 1.0 + 84.0 * q.e;
-      }
-      // the scaled V-cycle's coefficients (common.cuh): v = al u + be S + b'
-      q.wd = omega / q.d;
-      q.al = 1.0 - omega;
-      q.om = omega;
-      q.be = q.wd * q.e;
-      q.be2 = q.wd * q.e2;
-      q.a11w = q.wd * q.a11;
-      q.rs = k > 0 ? q.wd / cd[(size_t)(k - 1) * B + b].wd : 1.0;
+      const Coef<double> q =
+          mg_level_coef(order, cvals[b], h, k > 0 ? cd[(size_t)(k - 1) * B + b].wd : 0.0);
       cd[(size_t)k * B + b] = q;
       if (k == 0) c64[b] = q;
     }

@@ -161,7 +161,7 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map
 }
 
 template <typename T, int ORDER>
-__device__ __forceinline__ T combine(T s1, T s2) {
+__host__ __device__ __forceinline__ T combine(T s1, T s2) {
   if (ORDER == 2) return s1;
   return fma(T(16), s1, -s2);
 }
@@ -269,14 +269,14 @@ struct OpResid64 {
 // at all (a runtime branch is if-converted and would run the FP64 add
 // everywhere).
 template <typename T, int ORDER>
-__device__ __forceinline__ T jacobi_point(T al, T be, T be2, T c, T s1, T s2, T bp) {
+__host__ __device__ __forceinline__ T jacobi_point(T al, T be, T be2, T c, T s1, T s2, T bp) {
   if (ORDER == kCompact) return fma(al, c, fma(be, s1, fma(be2, s2, bp)));
   return fma(al, c, fma(be, combine<T, ORDER>(s1, s2), bp));
 }
 // t' = wd (b - A e) = b' - om e + be S (compact: + be2 S2), the residual the
 // restriction takes on the scaled levels.
 template <typename T, int ORDER>
-__device__ __forceinline__ T resid_point(T om, T be, T be2, T c, T s1, T s2, T bp) {
+__host__ __device__ __forceinline__ T resid_point(T om, T be, T be2, T c, T s1, T s2, T bp) {
   if (ORDER == kCompact) return fma(-om, c, fma(be, s1, fma(be2, s2, bp)));
   return fma(-om, c, fma(be, combine<T, ORDER>(s1, s2), bp));
 }
